@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput benchmark: search states/sec (and matches/sec) on one GB300.
+
+Default workload (the dense RI-DS configuration): target G(2000, 0.05) with
+4 uniform vertex labels, five dense-walk patterns of 16, 18, 20, 22 and 24
+vertices, RI-DS-SI-FC.  One step = one batched launch sequence over the five
+(target, pattern) pairs through the C ABI: domains (init, arc consistency,
+forward checking), ordering, breadth-first split and the persistent search.
+Inputs are resident in device memory before timing; L2 is flushed (256 MB
+write) between timed steps.  The line also carries the end-to-end number
+(host buffers in, results out, through the public API), the roofline of the
+persistent search kernel, the CPU oracle on a bounded sample, and the
+batched-vs-per-query speedup on a sample of the molecule workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of
+the workload (weak scaling); ranks exchange only the timing maximum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "search states/sec and matches/sec on 1 GB300; batched vs per-query speedup"
+UNIT = "states/s"
+WORKLOAD = ("er2000: ER G(2000, p=0.05) target, 4 uniform vertex labels, 5 dense-walk patterns "
+            "(16, 18, 20, 22, 24 vertices), RI-DS-SI-FC, all five pairs per step in one batched launch sequence")
+ALGO = 3
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 7:
+                        continue
+                    try:
+                        sm.append(float(parts[0]))
+                        mx.append(float(parts[1]))
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, parts[3:7]):
+                        if v.lower() == "active":
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    import torch
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+# ----------------------------------------------------------- CPU oracle leg
+def oracle_sample(workload, budget_per_pattern: int) -> dict:
+    """The oracle as it stands, one thread, on every pattern with a state budget."""
+    import oracle
+    t = workload.targets[0]
+    ot = oracle.Target(t)
+    states = matches = 0
+    t0 = time.perf_counter()
+    for p in workload.patterns:
+        r = oracle.run(ot, p, ALGO, state_budget=budget_per_pattern)
+        states += r["states"]
+        matches += r["matches"]
+    dt = time.perf_counter() - t0
+    return {"states": states, "matches": matches, "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    from gen import configs
+    if rank != 0:
+        return
+    w = configs.er2000()
+    budget = 10_000_000
+    for _ in range(args.warmup):
+        oracle_sample(w, budget)
+    tot_s = tot_t = tot_m = 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(w, budget)
+        tot_s += r["states"]
+        tot_m += r["matches"]
+        tot_t += r["seconds"]
+    value = tot_s / tot_t
+    sample = f"each step: the oracle on all 5 patterns, each stopped after {budget} states (bounded sample)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "matches_per_sec": tot_m / tot_t,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1705_09358_gb300 as sge
+    from gen import configs
+    sge.build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    w = configs.er2000()
+    t = w.targets[0]
+    E = sge.Context(local, stream=stream)
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in w.patterns]
+    tids = [tid] * len(pids)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def step():
+        rc, rows = E.count_batch(tids, pids, algo=ALGO)
+        return rows
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    states = matches = alg_bytes = launches = 0
+    kernel_ms = 0.0
+    kernel_launches = 0
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()                       # evict L2 between timed steps
+                ev[i][0].record(stream)
+                rows = step()
+                ev[i][1].record(stream)
+                states += int(rows["states"].sum())
+                matches += int(rows["matches"].sum())
+                alg_bytes += int(rows["alg_bytes"].sum())
+                launches += int(rows["launches"][0])
+                kernel_ms += float(rows["search_kernel_ms"][0])
+                kernel_launches += 1
+        barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    total_s = max_over_ranks(total_s, world)
+    value = world * states / total_s
+    peak, peak_kind = _peaks()
+    achieved = (alg_bytes / kernel_launches) / ((kernel_ms / kernel_launches) / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_search_bits<1> (persistent bitset search)",
+                "kernel_ms_per_launch": kernel_ms / kernel_launches,
+                "alg_bytes_per_launch": alg_bytes / kernel_launches, "peak_kind": f"of {peak_kind} HBM copy"}
+
+    # ------------------------------------------------------ end to end
+    srcs = [(p.n, p.src, p.dst, p.vlabel, p.elabel) for p in w.patterns]
+    h2d = 4 * (t.src.size + t.dst.size + t.vlabel.size) + sum(4 * (s.size + d.size + v.size) for _, s, d, v, _ in srcs)
+    d2h = len(w.patterns) * 128
+    e2e_steps = max(3, args.steps // 2)
+    e2e_states = 0
+    barrier(world)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            flush.zero_()
+            tt = sge.sge_load_target(E.h, t.n, t.src, t.dst, t.vlabel, t.elabel, False)
+            pp = [sge.sge_load_pattern(E.h, n, s, d, v, e, False) for n, s, d, v, e in srcs]
+            rc, rows = E.count_batch([tt] * len(pp), pp, algo=ALGO)
+            e2e_states += int(rows["states"].sum())
+            for x in pp:
+                sge.sge_unload_pattern(E.h, x)
+            sge.sge_unload_target(E.h, tt)
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * e2e_states / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h),
+           "note": "sge_load_target + 5 x sge_load_pattern from host arrays, sge_count_batch, results to host, unload"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "matches_per_sec": world * matches / total_s,
+            "states_per_step": states // args.steps, "matches_per_step": matches // args.steps,
+            "gpu_launches": launches, "roofline": roofline, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["batched_vs_per_query"] = batched_vs_per_query(E, args)
+        smp = oracle_sample(w, 60_000_000)
+        line["cpu_baseline"] = {"value": smp["states"] / smp["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "the oracle (one thread) on all 5 patterns, each stopped after 6e7 states; "
+                                          f"{smp['states']} states in {smp['seconds']:.1f} s"}
+    with Clocks(local) as _:
+        pass
+    line["clocks"] = clk.summary()
+    E.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def batched_vs_per_query(E, args) -> dict:
+    """Molecule workload sample: every pair in one batched call vs one call per pair."""
+    import torch
+    from gen import configs
+    ts = configs.mol_targets(200)[:20]
+    ps = configs.mol_patterns(configs.mol_targets(200), 1000)[:100]
+    tids = [E.load_target(t) for t in ts]
+    pids = [E.load_pattern(p) for p in ps]
+    T = np.repeat(np.array(tids, np.int32), len(pids))
+    P = np.tile(np.array(pids, np.int32), len(tids))
+    E.count_batch(T[:64], P[:64])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, rows = E.count_batch(T, P)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    sb = int(rows["states"].sum())
+    n_single = min(len(T), 400)
+    t0 = time.perf_counter()
+    s1 = 0
+    for i in range(n_single):
+        s1 += E.count(int(T[i]), int(P[i]))["states"]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter() - t0
+    b_rate, q_rate = sb / tb, s1 / t1
+    return {"pairs_batched": int(len(T)), "pairs_per_query_sample": n_single,
+            "batched_states_per_s": b_rate, "per_query_states_per_s": q_rate, "speedup": b_rate / q_rate,
+            "workload": "molecule-shaped: 20 targets x 100 patterns of the 200 x 1000 set, RI"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the CPU baseline and batched comparison")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

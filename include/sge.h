@@ -1,0 +1,197 @@
+/*
+ * sge.h -- C ABI of the GB300 subgraph-enumeration engine.
+ *
+ * The engine lists every non-induced labelled subgraph isomorphism (Kimmig,
+ * Meyerhenke, Strash, "Shared Memory Parallel Subgraph Enumeration", arXiv
+ * 1705.09358, Section 2.1, Eqs. 1-3): each injection f of the pattern's
+ * vertices into the target's vertices such that every pattern edge (u, v)
+ * is carried onto a target edge (f(u), f(v)) with an equal edge label and
+ * every pattern vertex onto a target vertex with an equal label.  The
+ * search is RI (Section "RI": GreatestConstraintFirst ordering, parent map,
+ * pruning rules 1-4) or RI-DS (Section 4: per-pattern-vertex target
+ * domains pruned by arc consistency), optionally with the paper's stronger
+ * pruning (Section 4.2: domain-size tie-break "SI" and forward checking of
+ * singleton domains "FC").  All compute runs in sm_103a CUDA kernels.
+ *
+ * Conventions for every call:
+ *  - Return value: SGE_OK (0) or a negative SGE_ERR_* code.  Nothing is
+ *    thrown across the ABI.  sge_last_error() gives a message for the last
+ *    failing call on that context.
+ *  - Host arrays passed in are borrowed for the duration of the call and
+ *    copied; the caller keeps ownership.  All device memory is owned by the
+ *    context and freed by sge_destroy().
+ *  - A context is used by one host thread at a time, except sge_cancel()
+ *    (any thread) and the serving calls (internally synchronised).
+ *  - Vertex ids are 0..n-1 (int32).  Labels are arbitrary int32 values
+ *    compared for equality; a NULL edge-label array means every edge has
+ *    label 0.
+ */
+#ifndef SGE_H
+#define SGE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sge_ctx sge_ctx;
+typedef int32_t sge_status;
+
+enum {
+    SGE_OK = 0,
+    SGE_ERR_ARG = -1,       /* invalid argument or input graph */
+    SGE_ERR_OOM = -2,       /* host or device allocation failed */
+    SGE_ERR_CUDA = -3,      /* a CUDA call failed (message in sge_last_error) */
+    SGE_ERR_BUDGET = -4,    /* opts.state_budget reached; counters are partial */
+    SGE_ERR_TIMEOUT = -5,   /* opts.time_limit_ms reached; counters are partial */
+    SGE_ERR_CANCELLED = -6, /* sge_cancel() was called; counters are partial */
+    SGE_ERR_STOPPED = -7,   /* the match sink asked to stop */
+    SGE_ERR_NOT_FOUND = -8  /* unknown target / pattern / ticket id */
+};
+
+/* Search variants (Section "RI" and Section 4). */
+enum {
+    SGE_RI = 0,         /* RI: candidates from V_t or the parent's adjacency */
+    SGE_RIDS = 1,       /* RI-DS: domains with arc consistency */
+    SGE_RIDS_SI = 2,    /* RI-DS + domain-size tie-break in the ordering */
+    SGE_RIDS_SI_FC = 3  /* RI-DS-SI + forward checking of singleton domains */
+};
+
+/* Kernel family used for the persistent search. */
+enum {
+    SGE_KERNEL_AUTO = 0,   /* bitset kernel when the target allows it, else CSR */
+    SGE_KERNEL_CSR = 1,    /* candidates streamed from sorted CSR rows */
+    SGE_KERNEL_BITSET = 2  /* candidates as word-parallel ANDs of adjacency bitsets */
+};
+
+/* Options; a zero field takes its default. */
+typedef struct {
+    int32_t algo;              /* SGE_RI .. SGE_RIDS_SI_FC (default SGE_RI) */
+    int32_t split_depth;       /* depth of the breadth-first split; 0 = auto */
+    int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 8) */
+    int32_t steal_granularity; /* most frames one donation hands out (default 8) */
+    int64_t state_budget;      /* stop after about this many states (0 = none) */
+    int64_t time_limit_ms;     /* stop after about this much search time (0 = none) */
+    int32_t kernel;            /* SGE_KERNEL_* */
+    int32_t blocks_per_sm;     /* persistent-kernel blocks per SM (0 = occupancy maximum) */
+    int32_t shard_index;       /* multi-device form: this device's shard ... */
+    int32_t shard_count;       /* ... of the split frontier (0 or 1 = unsharded) */
+    int32_t no_donation;       /* 1 = persistent kernel without work donation */
+    int32_t reserved[5];
+} sge_opts;
+
+/* Result of one (target, pattern) search.
+ *  matches: number of injections found.
+ *  states:  (pattern node, target node) pairs considered = sum over expanded
+ *           search nodes of the raw candidate-set size (Section 5, "search
+ *           space size").
+ *  nodes:   accepted pairs (search-tree nodes below the root, matches included).
+ *  hash:    sum over matches of h(f) mod 2^64, with
+ *           g(u, v) = fmix64(((u64)u << 32 | v) + 0x9E3779B97F4A7C15) and
+ *           h(f) = fmix64(sum_u g(u, f(u))), fmix64 the SplitMix64 finaliser.
+ * With shard_count > 1 the counters cover this shard only; summing them over
+ * all shards gives the unsharded result. */
+typedef struct {
+    uint64_t matches, states, nodes, hash;
+    double preprocess_ms;    /* domains, ordering, table upload (host clock) */
+    double match_ms;         /* split + persistent search (host clock) */
+    double search_kernel_ms; /* device time of the persistent search kernel (CUDA events) */
+    int64_t frames;          /* frontier frames handed to the persistent kernel */
+    int64_t donations;       /* frames donated between warps during the search */
+    uint64_t alg_bytes;      /* algorithmic bytes of the persistent search: bitset kernel:
+                                sum over expanded nodes of (rows ANDed) x ceil(n_t/64) x 8;
+                                CSR kernel: 12 per state (4-byte candidate id + 8-byte
+                                label/degree record) */
+    int64_t launches;        /* CUDA kernels this call launched */
+    int32_t split_depth;     /* depth of that frontier */
+    int32_t status;          /* SGE_OK or the error of this pair */
+    int32_t kernel;          /* SGE_KERNEL_CSR or SGE_KERNEL_BITSET as used */
+    int32_t reserved[3];
+} sge_result;
+
+/* Match sink: receives `count` matches, each k int32 target ids giving the
+ * images of pattern vertices 0..k-1.  The buffer is valid only during the
+ * call; calls come from the thread that called sge_enumerate.  Return
+ * nonzero to stop the enumeration (sge_enumerate then returns
+ * SGE_ERR_STOPPED).  Call order is unspecified. */
+typedef int (*sge_match_sink)(void *user, const int32_t *matches, int64_t count, int32_t k);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (for example the current PyTorch stream), or NULL for a stream
+ * the context creates.  Errors: ARG (bad device), CUDA, OOM. */
+sge_status sge_create(sge_ctx **out, int32_t device, void *cuda_stream);
+
+/* Free the context and every device buffer it owns.  NULL is allowed. */
+void sge_destroy(sge_ctx *ctx);
+
+/* Load a target graph (Section 2.1).  Edge e is (src[e], dst[e]) with label
+ * elabel[e] (NULL = all 0).  Undirected (directed = 0): each edge is given
+ * once in either orientation.  The graph is validated, repeated edges with an
+ * equal label are merged, and it is copied to device memory as sorted CSR
+ * rows (plus an adjacency bitset when small enough).
+ * Errors: ARG for n < 0, m < 0, an id out of range, a self-loop, a repeated
+ * edge with a different label, or more than 2^31 - 1 stored arcs; OOM; CUDA. */
+sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                           const int32_t *vlabel, const int32_t *elabel, int32_t directed,
+                           int32_t *target_id);
+
+/* Load a pattern graph; same arguments and errors as sge_load_target.
+ * Patterns have at most 128 vertices (ARG otherwise); the pattern and the
+ * target of a search must agree on `directed`. */
+sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                            const int32_t *vlabel, const int32_t *elabel, int32_t directed,
+                            int32_t *pattern_id);
+
+/* Release a loaded graph's device memory.  NOT_FOUND for an unknown id. */
+sge_status sge_unload_target(sge_ctx *ctx, int32_t target_id);
+sge_status sge_unload_pattern(sge_ctx *ctx, int32_t pattern_id);
+
+/* Count the matches of pattern `pattern_id` in target `target_id`.
+ * opts may be NULL (defaults).  A pattern with no vertices or more vertices
+ * than the target has no match and no search (all counters 0).  Errors: ARG,
+ * NOT_FOUND, OOM, CUDA, BUDGET / TIMEOUT / CANCELLED (out holds partial
+ * counters). */
+sge_status sge_count(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts,
+                     sge_result *out);
+
+/* As sge_count, and also pass every match to `sink` (called after the device
+ * search, in chunks).  Errors as sge_count, plus STOPPED. */
+sge_status sge_enumerate(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts,
+                         sge_match_sink sink, void *user, sge_result *out);
+
+/* Count `npairs` (target, pattern) pairs in one batched launch sequence: all
+ * pairs share one split and one persistent search kernel.  out[i] is the
+ * result of pair i (caller-owned array of npairs).  The return value is
+ * SGE_OK or the first error; per-pair errors are in out[i].status. */
+sge_status sge_count_batch(sge_ctx *ctx, int64_t npairs, const int32_t *target_ids,
+                           const int32_t *pattern_ids, const sge_opts *opts, sge_result *out);
+
+/* Serving (continuous batching).  sge_serve_submit queues one query and
+ * returns at once with a ticket; a scheduler thread owned by the context
+ * admits queued queries into free device slots as memory allows, launching
+ * each admitted group while earlier groups still run on other streams.
+ * sge_serve_poll sets *done = 1 and fills *out once the query finished
+ * (out->status holds its own error), else *done = 0.  Errors: ARG,
+ * NOT_FOUND. */
+sge_status sge_serve_submit(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts,
+                            int64_t *ticket);
+sge_status sge_serve_poll(sge_ctx *ctx, int64_t ticket, int32_t *done, sge_result *out);
+/* Block until every submitted query finished. */
+sge_status sge_serve_drain(sge_ctx *ctx);
+
+/* Ask the running search(es) to stop; they return SGE_ERR_CANCELLED.
+ * Callable from any thread. */
+sge_status sge_cancel(sge_ctx *ctx);
+
+/* Message for the last error on this context (never NULL). */
+const char *sge_last_error(sge_ctx *ctx);
+
+/* Library version string. */
+const char *sge_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGE_H */

@@ -1,0 +1,1163 @@
+// sge_host.cpp -- host side of the C ABI declared in include/sge.h.
+//
+// Graph ingest (validation, CSR build, adjacency bitsets), the GPU-host
+// statement of RI's GreatestConstraintFirst ordering (Section "RI") with the
+// RI-DS singleton block and SI tie-break (Section 4), the per-search position
+// tables, and the launch sequence: domains (RI-DS), breadth-first split,
+// persistent search.  All enumeration arithmetic runs in sge_kernels.cu; this
+// file only prepares tables and orchestrates launches.
+#include "../../include/sge.h"
+#include "sge_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+using namespace sge;
+
+namespace {
+
+constexpr int NO_ARC = INT_MIN;
+constexpr int BITSET_MAX_N = 16384;              // adjacency bitset kept for n <= this (<= 32 MB)
+constexpr long long FRONTIER_MAX_INTS = 1ll << 27;  // 512 MB per frontier buffer
+constexpr int POOL_CELLS = 1 << 15;
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------ device buffers
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t nb = bytes < 256 ? 256 : bytes;
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        cap = nb;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// -------------------------------------------------------------- graph build
+struct Rows {
+    std::vector<int32_t> ptr, col, lab;
+};
+
+struct Built {
+    int n = 0;
+    bool directed = false;
+    bool any_elab = false;
+    Rows out, in;   // in: directed only
+    std::vector<int32_t> vlab, odeg, ideg;
+};
+
+struct Arc {
+    uint64_t key;  // (a << 32) | b
+    int32_t lab;
+};
+
+// Sort arcs, merge repeats with an equal label; false on a conflicting repeat.
+bool rows_from_arcs(int n, std::vector<Arc> &arcs, Rows &r) {
+    std::sort(arcs.begin(), arcs.end(), [](const Arc &x, const Arc &y) { return x.key < y.key; });
+    size_t w = 0;
+    for (size_t i = 0; i < arcs.size(); ++i) {
+        if (w > 0 && arcs[w - 1].key == arcs[i].key) {
+            if (arcs[w - 1].lab != arcs[i].lab) return false;
+            continue;
+        }
+        arcs[w++] = arcs[i];
+    }
+    arcs.resize(w);
+    r.ptr.assign((size_t)n + 1, 0);
+    r.col.resize(w);
+    r.lab.resize(w);
+    for (size_t i = 0; i < w; ++i) {
+        const int a = (int)(arcs[i].key >> 32);
+        r.ptr[(size_t)a + 1]++;
+        r.col[i] = (int32_t)(arcs[i].key & 0xffffffffu);
+        r.lab[i] = arcs[i].lab;
+    }
+    for (int v = 0; v < n; ++v) r.ptr[(size_t)v + 1] += r.ptr[v];
+    return true;
+}
+
+bool build_graph(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *vlabel,
+                 const int32_t *elabel, int directed, Built &g, std::string &err) {
+    if (n < 0 || m < 0) { err = "negative vertex or edge count"; return false; }
+    if (m > 0 && (!src || !dst)) { err = "null edge arrays"; return false; }
+    if (n > 0 && !vlabel) { err = "null vertex-label array"; return false; }
+    if ((directed ? m : 2 * m) > INT32_MAX) { err = "more than 2^31-1 stored arcs"; return false; }
+    g.n = n;
+    g.directed = directed != 0;
+    std::vector<Arc> out, in;
+    out.reserve(g.directed ? (size_t)m : 2 * (size_t)m);
+    if (g.directed) in.reserve((size_t)m);
+    for (int64_t e = 0; e < m; ++e) {
+        const int a = src[e], b = dst[e];
+        const int l = elabel ? elabel[e] : 0;
+        if (a < 0 || a >= n || b < 0 || b >= n) { err = "edge endpoint out of range"; return false; }
+        if (a == b) { err = "self-loop"; return false; }
+        if (l != 0) g.any_elab = true;
+        out.push_back({(uint64_t)(uint32_t)a << 32 | (uint32_t)b, l});
+        if (g.directed) in.push_back({(uint64_t)(uint32_t)b << 32 | (uint32_t)a, l});
+        else out.push_back({(uint64_t)(uint32_t)b << 32 | (uint32_t)a, l});
+    }
+    if (!rows_from_arcs(n, out, g.out) || (g.directed && !rows_from_arcs(n, in, g.in))) {
+        err = "repeated edge with a different label";
+        return false;
+    }
+    g.vlab.assign(vlabel, vlabel + n);
+    g.odeg.resize(n);
+    g.ideg.resize(n);
+    for (int v = 0; v < n; ++v) {
+        g.odeg[v] = g.out.ptr[v + 1] - g.out.ptr[v];
+        g.ideg[v] = g.directed ? g.in.ptr[v + 1] - g.in.ptr[v] : g.odeg[v];
+    }
+    return true;
+}
+
+// --------------------------------------------------------------- contexts
+struct TargetRec {
+    int n = 0, dw = 0;
+    bool directed = false, any_elab = false;
+    long long nnz = 0;
+    DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj;
+    TargetView view() const {
+        TargetView v;
+        v.n = n;
+        v.dw = dw;
+        v.rowptr = rowptr.as<int32_t>();
+        v.col = col.as<int32_t>();
+        v.elab = elab.as<int32_t>();
+        // undirected: the in-rows are the rows themselves
+        v.irowptr = directed ? irowptr.as<int32_t>() : v.rowptr;
+        v.icol = directed ? icol.as<int32_t>() : v.col;
+        v.ielab = directed ? ielab.as<int32_t>() : v.elab;
+        v.vld = vld.as<int2>();
+        v.indeg = directed ? indeg.as<int32_t>() : nullptr;
+        v.adj = adj.p ? adj.as<uint64_t>() : nullptr;
+        return v;
+    }
+    void release() {
+        for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj}) b->release();
+    }
+};
+
+struct PatternRec {
+    int k = 0;
+    bool directed = false, any_elab = false;
+    std::vector<int32_t> lab, odeg, ideg;
+    std::vector<int> amat;                 // k x k arc labels, NO_ARC if absent
+    std::vector<std::vector<uint64_t>> nb; // undirected neighbourhood bitsets (2 words, k <= 128)
+    std::vector<int> ri_mu, ri_par;        // cached RI ordering
+    DevBuf dlab, dodeg, dideg, drow, dcol, delab, dirow, dicol, dielab;
+    PatternView view() const {
+        PatternView v;
+        v.k = k;
+        v.pad = 0;
+        v.lab = dlab.as<int32_t>();
+        v.odeg = dodeg.as<int32_t>();
+        v.ideg = directed ? dideg.as<int32_t>() : dodeg.as<int32_t>();
+        v.rowptr = drow.as<int32_t>();
+        v.col = dcol.as<int32_t>();
+        v.elab = delab.as<int32_t>();
+        v.irowptr = directed ? dirow.as<int32_t>() : v.rowptr;
+        v.icol = directed ? dicol.as<int32_t>() : v.col;
+        v.ielab = directed ? dielab.as<int32_t>() : v.elab;
+        return v;
+    }
+    void release() {
+        for (DevBuf *b : {&dlab, &dodeg, &dideg, &drow, &dcol, &delab, &dirow, &dicol, &dielab}) b->release();
+    }
+};
+
+// Scratch of one launch sequence (the serving scheduler has one per slot).
+struct Workspace {
+    DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag;
+    DevBuf front[2], counts, offs, scan_tmp, total;
+    DevBuf pool, pseq, ctl;
+    DevBuf mbuf;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void release() {
+        for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
+                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &pool, &pseq, &ctl, &mbuf})
+            b->release();
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        ev0 = ev1 = nullptr;
+    }
+};
+
+struct ServeReq;
+
+}  // namespace
+
+struct sge_ctx {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::map<int, std::unique_ptr<TargetRec>> targets;
+    std::map<int, std::unique_ptr<PatternRec>> patterns;
+    int next_target = 1, next_pattern = 1;
+    std::string err;
+    std::mutex mu;               // guards targets / patterns / err for the serving thread
+    int *cancel_host = nullptr;  // mapped pinned word
+    int *cancel_dev = nullptr;
+    Workspace ws;
+    // serving
+    std::mutex smu;
+    std::condition_variable scv;
+    std::deque<std::shared_ptr<ServeReq>> squeue;
+    std::map<int64_t, std::shared_ptr<ServeReq>> sreqs;
+    int64_t next_ticket = 1;
+    std::vector<std::thread> sworkers;
+    bool sstop = false;
+    int sinflight = 0;
+    long long sbytes_in_use = 0;
+};
+
+namespace {
+
+struct ServeReq {
+    int32_t tid, pid;
+    sge_opts opts;
+    sge_result res;
+    bool done = false;
+    long long bytes = 0;
+};
+
+sge_status fail(sge_ctx *ctx, sge_status code, const std::string &msg) {
+    if (ctx) {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->err = msg;
+    }
+    return code;
+}
+
+sge_status cuda_fail(sge_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? SGE_ERR_OOM : SGE_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+template <class T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
+    cudaError_t e = b.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// ------------------------------------------------------------- ordering
+// GreatestConstraintFirst (Section "RI"): the first vertex has the highest
+// degree, then greedily the vertex with most neighbours in mu (w_m), then most
+// vertices of mu reachable through one vertex outside mu (w_n), then highest
+// degree; RI-DS puts singleton domains first (ascending id) and SI breaks the
+// remaining ties by the smaller domain (Section 4.1).  Lower id last.
+// Neighbourhoods ignore edge direction.
+struct OrderKey {
+    long wm, wn, deg;
+    long long dsz;
+};
+
+void gcf_order(const PatternRec &P, int algo, const long long *dsize, std::vector<int> &mu, std::vector<int> &par) {
+    const int k = P.k;
+    const bool si = algo == SGE_RIDS_SI || algo == SGE_RIDS_SI_FC;
+    uint64_t in[2] = {0, 0};
+    auto has = [&](const uint64_t *s, int v) { return (s[v >> 6] >> (v & 63)) & 1ull; };
+    auto deg = [&](int v) -> long { return P.odeg[v] + (P.directed ? P.ideg[v] : 0); };
+    mu.clear();
+    if (algo != SGE_RI)
+        for (int v = 0; v < k; ++v)
+            if (dsize[v] == 1) { mu.push_back(v); in[v >> 6] |= 1ull << (v & 63); }
+    if (mu.empty() && k > 0) {
+        int best = 0;
+        for (int v = 1; v < k; ++v) {
+            const long dv = deg(v), db = deg(best);
+            if (dv > db || (dv == db && si && dsize[v] < dsize[best])) best = v;
+        }
+        mu.push_back(best);
+        in[best >> 6] |= 1ull << (best & 63);
+    }
+    while ((int)mu.size() < k) {
+        int best = -1;
+        OrderKey bk{0, 0, 0, 0};
+        for (int v = 0; v < k; ++v) {
+            if (has(in, v)) continue;
+            const uint64_t *nv = P.nb[v].data();
+            OrderKey key;
+            key.wm = __builtin_popcountll(nv[0] & in[0]) + __builtin_popcountll(nv[1] & in[1]);
+            // vertices of mu adjacent to some neighbour x of v outside mu
+            uint64_t reach[2] = {0, 0};
+            for (int h = 0; h < 2; ++h) {
+                uint64_t outside = nv[h] & ~in[h];
+                while (outside) {
+                    const int x = h * 64 + __builtin_ctzll(outside);
+                    outside &= outside - 1;
+                    reach[0] |= P.nb[x][0];
+                    reach[1] |= P.nb[x][1];
+                }
+            }
+            key.wn = __builtin_popcountll(reach[0] & in[0]) + __builtin_popcountll(reach[1] & in[1]);
+            key.deg = deg(v);
+            key.dsz = si ? dsize[v] : 0;
+            bool take = best < 0;
+            if (!take) {
+                if (key.wm != bk.wm) take = key.wm > bk.wm;
+                else if (key.wn != bk.wn) take = key.wn > bk.wn;
+                else if (key.deg != bk.deg) take = key.deg > bk.deg;
+                else if (key.dsz != bk.dsz) take = key.dsz < bk.dsz;
+            }
+            if (take) { best = v; bk = key; }
+        }
+        mu.push_back(best);
+        in[best >> 6] |= 1ull << (best & 63);
+    }
+    // parent: the earliest earlier vertex adjacent to mu_i
+    par.assign(k, -1);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < i; ++j)
+            if (has(P.nb[mu[i]].data(), mu[j])) { par[i] = j; break; }
+}
+
+// Position tables of one search from its ordering (rules 2-4 per position).
+void build_positions(const PatternRec &P, const std::vector<int> &mu, const std::vector<int> &par, int algo,
+                     const long long *dsize, int n, std::vector<PosInfo> &pos, std::vector<BackEdge> &back) {
+    const int k = P.k;
+    pos.resize(k);
+    std::vector<int> at(k);
+    for (int i = 0; i < k; ++i) at[mu[i]] = i;
+    for (int i = 0; i < k; ++i) {
+        const int v = mu[i];
+        PosInfo &p = pos[i];
+        std::memset(&p, 0, sizeof(p));
+        p.pv = v;
+        p.par = par[i];
+        p.lab = P.lab[v];
+        p.odeg = P.odeg[v];
+        p.ideg = P.directed ? P.ideg[v] : 0;
+        p.uoff = -1;
+        if (p.par >= 0) {
+            const int u = mu[p.par];
+            if (!P.directed || P.amat[(size_t)u * k + v] != NO_ARC) {
+                p.pel = P.amat[(size_t)u * k + v];           // arc P -> mu_i: out-row of M(P)
+            } else {
+                p.flags |= POS_IN_ROW;                         // arc mu_i -> P: in-row of M(P)
+                p.pel = P.amat[(size_t)v * k + u];
+            }
+        } else {
+            p.ucnt = algo == SGE_RI ? n : (int)dsize[v];
+        }
+        p.bbeg = (int)back.size();
+        for (int j = 0; j < i; ++j) {
+            const int w = mu[j];
+            const int lo = P.amat[(size_t)v * k + w], li = P.amat[(size_t)w * k + v];
+            bool need_out = lo != NO_ARC, need_in = li != NO_ARC;
+            if (!need_out && !need_in) continue;
+            if (j == p.par) {
+                if (!P.directed) continue;                      // the row itself is this edge
+                if (p.flags & POS_IN_ROW) need_out = false; else need_in = false;
+                if (!need_out && !need_in) continue;
+            }
+            BackEdge be;
+            be.pos = j;
+            be.dir = P.directed ? ((need_out ? 1 : 0) | (need_in ? 2 : 0)) : 1;
+            be.lab_out = need_out ? lo : 0;
+            be.lab_in = need_in ? li : 0;
+            back.push_back(be);
+        }
+        p.bcnt = (int)back.size() - p.bbeg;
+    }
+    (void)at;
+}
+
+struct Job {
+    int pair;        // index into the request
+    TargetRec *t;
+    PatternRec *p;
+    int algo;
+    bool active;
+    long long filt_off = -1;  // offset (u64 words) of the job's filter block
+    long long vert_off = 0;   // offset in the sizes array
+    std::vector<int> mu, par;
+    std::vector<long long> dsize;
+};
+
+struct PairReq {
+    int32_t tid, pid;
+};
+
+int pow2_at_least(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Run a homogeneous group of pairs (same directedness) through the whole
+// launch sequence on `st` with workspace `W`.
+sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
+                     const std::vector<int> &idx, const sge_opts &o, sge_result *out, bool enumerate,
+                     std::vector<int32_t> *match_rows, long long match_cap) {
+    const double t_start = now_ms();
+    long long launches = 0;   // kernels launched by this call
+    const int algo = o.algo;
+    const int nj = (int)idx.size();
+    std::vector<Job> jobs(nj);
+    bool directed = false, any_elab = false;
+    int kmax = 1, nmax = 1;
+    for (int q = 0; q < nj; ++q) {
+        Job &J = jobs[q];
+        J.pair = idx[q];
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            J.t = ctx->targets.at(reqs[J.pair].tid).get();
+            J.p = ctx->patterns.at(reqs[J.pair].pid).get();
+        }
+        J.algo = algo;
+        J.active = J.p->k > 0 && J.p->k <= J.t->n;
+        directed = J.t->directed;
+        if (J.active) {
+            kmax = std::max(kmax, J.p->k);
+            nmax = std::max(nmax, J.t->n);
+            any_elab = any_elab || J.t->any_elab || J.p->any_elab;
+        }
+    }
+    // kernel family: the bitset kernel needs undirected, unlabelled edges, an
+    // adjacency bitset and at most 4 words per lane with the level stack in
+    // shared memory
+    bool bits_ok = !directed && !any_elab;
+    int nwl = 1;
+    for (const Job &J : jobs)
+        if (J.active) {
+            if (!J.t->adj.p) bits_ok = false;
+            nwl = std::max(nwl, pow2_at_least((J.t->dw + 31) / 32));
+        }
+    if (nwl > 4 || search_smem_bytes(2, kmax, nwl) > 160 * 1024) bits_ok = false;
+    int kernel = SGE_KERNEL_CSR;
+    if (o.kernel == SGE_KERNEL_BITSET) {
+        if (!bits_ok) return fail(ctx, SGE_ERR_ARG, "bitset kernel requested but a pair does not allow it");
+        kernel = SGE_KERNEL_BITSET;
+    } else if (o.kernel == SGE_KERNEL_AUTO && bits_ok) {
+        kernel = SGE_KERNEL_BITSET;
+    }
+    const bool need_filt_all = kernel == SGE_KERNEL_BITSET;
+
+    // ---------------------------------------------------------- job tables
+    long long filt_words = 0, nverts = 0, nunits = 0;
+    std::vector<long long> unit_off, vert_off;
+    for (Job &J : jobs) {
+        if (!J.active) continue;
+        if (J.algo != SGE_RI || need_filt_all) {
+            J.filt_off = filt_words;
+            filt_words += (long long)J.p->k * J.t->dw;
+        }
+    }
+    std::vector<JobDesc> desc(nj);
+    CK(W.filt.ensure(std::max<long long>(filt_words, 1) * 8), "alloc filter");
+    // per job: 4 counters, then nj match-row counts, then nj byte counters
+    CK(W.ctr.ensure((size_t)nj * 6 * sizeof(unsigned long long)), "alloc counters");
+    CK(cudaMemsetAsync(W.ctr.p, 0, (size_t)nj * 6 * sizeof(unsigned long long), st), "clear counters");
+    for (int q = 0; q < nj; ++q) {
+        Job &J = jobs[q];
+        JobDesc &D = desc[q];
+        std::memset(&D, 0, sizeof(D));
+        D.t = J.t->view();
+        D.p = J.p->view();
+        D.k = J.p->k;
+        D.flags = (J.algo != SGE_RI ? JOB_RIDS : 0) | (any_elab ? JOB_ELAB : 0) | (directed ? JOB_DIRECTED : 0) |
+                  (J.algo == SGE_RIDS_SI_FC ? JOB_FC : 0);
+        D.ctr = W.ctr.as<unsigned long long>() + 4 * (size_t)q;
+        D.mlen = W.ctr.as<unsigned long long>() + 4 * (size_t)nj + q;
+        D.abytes = W.ctr.as<unsigned long long>() + 5 * (size_t)nj + q;
+        D.filt = J.filt_off >= 0 ? W.filt.as<uint64_t>() + J.filt_off : nullptr;
+    }
+    // units of the domain kernels: (job, pattern vertex, 64-target word)
+    std::vector<int> fjobs;  // jobs with a filter block, in order
+    for (int q = 0; q < nj; ++q)
+        if (jobs[q].active && jobs[q].filt_off >= 0) fjobs.push_back(q);
+    std::vector<JobDesc> fdesc;
+    for (int q : fjobs) {
+        unit_off.push_back(nunits);
+        vert_off.push_back(nverts);
+        jobs[q].vert_off = nverts;
+        nunits += (long long)jobs[q].p->k * jobs[q].t->dw;
+        nverts += jobs[q].p->k;
+        fdesc.push_back(desc[q]);
+    }
+    const int nf = (int)fjobs.size();
+    if (nf > 0) {
+        CK(upload(W.fjobs, fdesc, st), "upload domain jobs");
+        CK(upload(W.unit_off, unit_off, st), "upload unit offsets");
+        CK(upload(W.vert_off, vert_off, st), "upload vertex offsets");
+        CK(W.sizes.ensure((size_t)nverts * 8), "alloc sizes");
+        CK(W.flag.ensure(64), "alloc flag");
+        CK(launch_domain_init(W.fjobs.as<JobDesc>(), W.unit_off.as<long long>(), nf, nunits, st), "domain init");
+        ++launches;
+        bool any_rids = false, any_fc = false;
+        for (int q : fjobs) {
+            any_rids = any_rids || jobs[q].algo != SGE_RI;
+            any_fc = any_fc || jobs[q].algo == SGE_RIDS_SI_FC;
+        }
+        if (any_rids) {
+            // arc consistency to its fixpoint, alternating with forward checking
+            for (int outer = 0; outer < 100000; ++outer) {
+                int changed = 1;
+                for (int sweep = 0; changed && sweep < 1000000; ++sweep) {
+                    CK(cudaMemsetAsync(W.flag.p, 0, sizeof(int), st), "clear flag");
+                    CK(launch_domain_ac(W.fjobs.as<JobDesc>(), W.unit_off.as<long long>(), nf, nunits,
+                                        W.flag.as<int>(), st), "domain ac");
+                    ++launches;
+                    CK(cudaMemcpyAsync(&changed, W.flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+                    CK(cudaStreamSynchronize(st), "ac sync");
+                }
+                if (!any_fc) break;
+                int fchanged = 0;
+                CK(cudaMemsetAsync(W.flag.p, 0, sizeof(int), st), "clear flag");
+                CK(launch_domain_fc(W.fjobs.as<JobDesc>(), nf, W.flag.as<int>(), st), "domain fc");
+                ++launches;
+                CK(cudaMemcpyAsync(&fchanged, W.flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+                CK(cudaStreamSynchronize(st), "fc sync");
+                if (!fchanged) break;
+            }
+        }
+        CK(launch_domain_sizes(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts,
+                               W.sizes.as<long long>(), st), "domain sizes");
+        ++launches;
+        std::vector<long long> sizes((size_t)nverts);
+        CK(cudaMemcpyAsync(sizes.data(), W.sizes.p, (size_t)nverts * 8, cudaMemcpyDeviceToHost, st), "read sizes");
+        CK(cudaStreamSynchronize(st), "sizes sync");
+        for (int q : fjobs) {
+            Job &J = jobs[q];
+            J.dsize.assign(sizes.begin() + J.vert_off, sizes.begin() + J.vert_off + J.p->k);
+            if (J.algo != SGE_RI)
+                for (long long s : J.dsize)
+                    if (s == 0) J.active = false;   // an empty domain: no match, no search
+        }
+    }
+    // orderings and position tables
+    std::vector<PosInfo> pos;
+    std::vector<BackEdge> back;
+    std::vector<long long> pos_off(nj, 0), back_off(nj, 0);
+    std::vector<int> task_job, task_vert, task_out;
+    long long ulist_len = 0;
+    for (int q = 0; q < nj; ++q) {
+        Job &J = jobs[q];
+        if (!J.active) continue;
+        if (J.algo == SGE_RI) {
+            J.mu = J.p->ri_mu;
+            J.par = J.p->ri_par;
+        } else {
+            gcf_order(*J.p, J.algo, J.dsize.data(), J.mu, J.par);
+        }
+        pos_off[q] = (long long)pos.size();
+        back_off[q] = (long long)back.size();
+        std::vector<PosInfo> pq;
+        std::vector<BackEdge> bq;
+        build_positions(*J.p, J.mu, J.par, J.algo, J.dsize.empty() ? nullptr : J.dsize.data(), J.t->n, pq, bq);
+        for (PosInfo &p : pq) {
+            if (p.par < 0 && J.algo != SGE_RI) {
+                p.uoff = (int)ulist_len;
+                // the D(mu_i) list is written by a kernel below
+                int fq = -1;
+                for (int x = 0; x < nf; ++x)
+                    if (fjobs[x] == q) { fq = x; break; }
+                task_job.push_back(fq);
+                task_vert.push_back(p.pv);
+                task_out.push_back((int)ulist_len);
+                ulist_len += p.ucnt;
+            }
+        }
+        pos.insert(pos.end(), pq.begin(), pq.end());
+        back.insert(back.end(), bq.begin(), bq.end());
+    }
+    if (ulist_len > INT32_MAX) return fail(ctx, SGE_ERR_OOM, "unparented candidate lists too large");
+    CK(upload(W.pos, pos, st), "upload positions");
+    CK(upload(W.back, back, st), "upload back edges");
+    CK(W.ulist.ensure((size_t)std::max<long long>(ulist_len, 1) * 4), "alloc lists");
+    if (!task_job.empty()) {
+        std::vector<int> tasks;
+        tasks.insert(tasks.end(), task_job.begin(), task_job.end());
+        tasks.insert(tasks.end(), task_vert.begin(), task_vert.end());
+        tasks.insert(tasks.end(), task_out.begin(), task_out.end());
+        CK(upload(W.task, tasks, st), "upload list tasks");
+        const int nt = (int)task_job.size();
+        CK(launch_domain_lists(W.fjobs.as<JobDesc>(), W.task.as<int>(), W.task.as<int>() + nt,
+                               W.task.as<int>() + 2 * nt, nt, W.ulist.as<int32_t>(), st), "domain lists");
+        ++launches;
+    }
+    // enumeration output
+    if (enumerate) {
+        const long long rows = std::max<long long>(match_cap, 1);
+        CK(W.mbuf.ensure((size_t)rows * kmax * 4), "alloc match buffer");
+    }
+    for (int q = 0; q < nj; ++q) {
+        JobDesc &D = desc[q];
+        D.pos = W.pos.as<PosInfo>() + pos_off[q];
+        D.back = W.back.as<BackEdge>() + back_off[q];
+        D.ulist = W.ulist.as<int32_t>();
+        if (enumerate) {
+            D.mbuf = W.mbuf.as<int32_t>();
+            D.mcap = match_cap;
+        }
+    }
+    CK(upload(W.jobs, desc, st), "upload jobs");
+    const double t_pre = now_ms();
+
+    // -------------------------------------------------------- split (BFS)
+    const int shard_count = o.shard_count > 1 ? o.shard_count : 1;
+    const int shard_index = shard_count > 1 ? o.shard_index : 0;
+    const int count_ctr = shard_index == 0 ? 1 : 0;
+    int occ = 0;
+    CK(search_blocks_per_sm(kernel == SGE_KERNEL_BITSET ? 2 : 1, kmax, nwl, directed ? 1 : 0, &occ), "occupancy");
+    if (o.blocks_per_sm > 0 && o.blocks_per_sm < occ) occ = o.blocks_per_sm;
+    const long long resident_warps = (long long)ctx->sms * occ * search_warps_per_block();
+    const long long fpw = o.frames_per_warp > 0 ? o.frames_per_warp : 8;
+    const long long target_frames = fpw * resident_warps * shard_count;
+    std::vector<int32_t> f0;
+    for (int q = 0; q < nj; ++q)
+        if (jobs[q].active) { f0.push_back(q); f0.push_back(0); f0.push_back(-1); f0.push_back(-1); }
+    long long F = (long long)f0.size() / FRAME_HDR;
+    int cur = 0, depth = 0;
+    if (F > 0) CK(upload(W.front[0], f0, st), "upload roots");
+    while (F > 0) {
+        if (o.split_depth > 0) {
+            if (depth >= o.split_depth) break;
+        } else if (F >= target_frames) {
+            break;
+        }
+        if (depth >= kmax - 1) break;   // leave the last position to the search kernel
+        CK(W.counts.ensure((size_t)F * 4), "alloc counts");
+        CK(W.offs.ensure((size_t)F * 8), "alloc offsets");
+        CK(W.scan_tmp.ensure(scan_tmp_bytes(F)), "alloc scan");
+        CK(W.total.ensure(16), "alloc total");
+        CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(), nullptr,
+                        nullptr, 0, count_ctr, directed ? 1 : 0, st), "split count");
+        launches += 4;   // split count + three scan kernels
+        CK(launch_scan(W.counts.as<int32_t>(), W.offs.as<long long>(), F, W.total.as<long long>(), W.scan_tmp.p,
+                       W.scan_tmp.cap, st), "split scan");
+        long long total = 0;
+        CK(cudaMemcpyAsync(&total, W.total.p, 8, cudaMemcpyDeviceToHost, st), "read split total");
+        CK(cudaStreamSynchronize(st), "split sync");
+        const long long need = total * (FRAME_HDR + depth + 1);
+        if (need > FRONTIER_MAX_INTS) break;   // keep the current frontier
+        CK(W.front[cur ^ 1].ensure((size_t)std::max<long long>(need, 1) * 4), "alloc frontier");
+        CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(),
+                        W.offs.as<long long>(), W.front[cur ^ 1].as<int32_t>(), 1, count_ctr, directed ? 1 : 0, st),
+           "split write");
+        ++launches;
+        cur ^= 1;
+        F = total;
+        ++depth;
+    }
+
+    // ------------------------------------------------- persistent search
+    long long nfront = 0;
+    if (F > shard_index) nfront = (F - shard_index + shard_count - 1) / shard_count;
+    float kernel_ms = 0.f;
+    long long donations = 0;
+    int status = 0;
+    if (nfront > 0) {
+        CK(W.pool.ensure((size_t)POOL_CELLS * POOL_STRIDE * 4), "alloc pool");
+        CK(W.pseq.ensure((size_t)POOL_CELLS * 8), "alloc pool seq");
+        CK(W.ctl.ensure(64 * 8), "alloc control");
+        CK(cudaMemsetAsync(W.ctl.p, 0, 64 * 8, st), "clear control");
+        CK(launch_pool_init(W.pseq.as<unsigned long long>(), POOL_CELLS, st), "pool init");
+        ++launches;
+        unsigned long long *c64 = W.ctl.as<unsigned long long>();
+        SearchCtl C;
+        std::memset(&C, 0, sizeof(C));
+        C.front = W.front[cur].as<int32_t>();
+        C.nfront = nfront;
+        C.fstride = FRAME_HDR + depth;
+        C.shard_index = shard_index;
+        C.shard_count = shard_count;
+        C.pcap = POOL_CELLS;
+        C.fnext = c64 + 0;
+        C.pool = W.pool.as<int32_t>();
+        C.pseq = W.pseq.as<unsigned long long>();
+        C.phead = c64 + 1;
+        C.ptail = c64 + 2;
+        C.donations = c64 + 3;
+        int *c32 = reinterpret_cast<int *>(c64 + 8);
+        C.outstanding = c32 + 0;
+        C.idle = c32 + 1;
+        C.status = c32 + 2;
+        const int nf32 = (int)nfront;
+        CK(cudaMemcpyAsync(C.outstanding, &nf32, sizeof(int), cudaMemcpyHostToDevice, st), "init outstanding");
+        C.cancel = ctx->cancel_dev;
+        C.deadline_ns = o.time_limit_ms > 0 ? (unsigned long long)o.time_limit_ms * 1000000ull : 0ull;
+        C.budget = o.state_budget;
+        C.donate = o.no_donation ? 0 : 1;
+        C.gran = o.steal_granularity > 0 ? o.steal_granularity : 8;
+        if (!W.ev0) {
+            CK(cudaEventCreate(&W.ev0), "event");
+            CK(cudaEventCreate(&W.ev1), "event");
+        }
+        int grid = 0;
+        CK(cudaEventRecord(W.ev0, st), "event record");
+        CK(launch_search(kernel == SGE_KERNEL_BITSET ? 2 : 1, W.jobs.as<JobDesc>(), C, kmax, nwl, directed ? 1 : 0,
+                         o.blocks_per_sm, &grid, st), "search launch");
+        ++launches;
+        CK(cudaEventRecord(W.ev1, st), "event record");
+        unsigned long long dn = 0;
+        CK(cudaMemcpyAsync(&status, C.status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
+        CK(cudaMemcpyAsync(&dn, C.donations, 8, cudaMemcpyDeviceToHost, st), "read donations");
+        CK(cudaStreamSynchronize(st), "search sync");
+        CK(cudaEventElapsedTime(&kernel_ms, W.ev0, W.ev1), "event time");
+        donations = (long long)dn;
+    }
+    std::vector<unsigned long long> ctr((size_t)nj * 6);
+    CK(cudaMemcpyAsync(ctr.data(), W.ctr.p, (size_t)nj * 6 * 8, cudaMemcpyDeviceToHost, st), "read counters");
+    CK(cudaStreamSynchronize(st), "counter sync");
+    const double t_end = now_ms();
+    for (int q = 0; q < nj; ++q) {
+        sge_result &r = out[jobs[q].pair];
+        std::memset(&r, 0, sizeof(r));
+        r.matches = ctr[4 * (size_t)q + 0];
+        r.states = ctr[4 * (size_t)q + 1];
+        r.nodes = ctr[4 * (size_t)q + 2];
+        r.hash = ctr[4 * (size_t)q + 3];
+        r.preprocess_ms = t_pre - t_start;
+        r.match_ms = t_end - t_pre;
+        r.search_kernel_ms = kernel_ms;
+        r.frames = F;
+        r.donations = donations;
+        r.alg_bytes = kernel == SGE_KERNEL_BITSET ? ctr[5 * (size_t)nj + q] : 12ull * r.states;
+        r.launches = launches;
+        r.split_depth = depth;
+        r.status = status;
+        r.kernel = kernel;
+    }
+    if (enumerate && match_rows && nj == 1) {
+        const long long produced = (long long)ctr[4 * (size_t)nj + 0];
+        const long long rows = std::min(produced, match_cap);
+        match_rows->resize((size_t)rows * jobs[0].p->k);
+        if (rows > 0)
+            CK(cudaMemcpy(match_rows->data(), W.mbuf.p, (size_t)rows * jobs[0].p->k * 4, cudaMemcpyDeviceToHost),
+               "read matches");
+    }
+    if (status != 0) {
+        const char *why = status == SGE_ERR_BUDGET ? "state budget reached"
+                          : status == SGE_ERR_TIMEOUT ? "time limit reached"
+                          : status == SGE_ERR_CANCELLED ? "cancelled" : "search error";
+        return fail(ctx, status, why);
+    }
+    return SGE_OK;
+}
+
+sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
+                     const sge_opts *opts, sge_result *out, bool enumerate, std::vector<int32_t> *rows,
+                     long long cap) {
+    sge_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.time_limit_ms <= 0) {
+        // a process-wide default limit (SGE_TIME_LIMIT_MS) when the call sets none
+        const char *env = std::getenv("SGE_TIME_LIMIT_MS");
+        if (env) o.time_limit_ms = std::atoll(env);
+    }
+    if (o.algo < SGE_RI || o.algo > SGE_RIDS_SI_FC) return fail(ctx, SGE_ERR_ARG, "unknown algo");
+    if (o.kernel < 0 || o.kernel > 2) return fail(ctx, SGE_ERR_ARG, "unknown kernel family");
+    if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count))
+        return fail(ctx, SGE_ERR_ARG, "shard index out of range");
+    std::vector<int> und, dir;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (size_t i = 0; i < reqs.size(); ++i) {
+            auto ti = ctx->targets.find(reqs[i].tid);
+            auto pi = ctx->patterns.find(reqs[i].pid);
+            if (ti == ctx->targets.end() || pi == ctx->patterns.end()) {
+                ctx->err = "unknown target or pattern id";
+                return SGE_ERR_NOT_FOUND;
+            }
+            if (ti->second->directed != pi->second->directed) {
+                ctx->err = "target and pattern disagree on directedness";
+                return SGE_ERR_ARG;
+            }
+            (ti->second->directed ? dir : und).push_back((int)i);
+        }
+    }
+    sge_status rc = SGE_OK;
+    if (!und.empty()) rc = run_group(ctx, W, st, reqs, und, o, out, enumerate, rows, cap);
+    if (rc == SGE_OK && !dir.empty()) rc = run_group(ctx, W, st, reqs, dir, o, out, enumerate, rows, cap);
+    return rc;
+}
+
+sge_status load_graph_common(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                             const int32_t *vlabel, const int32_t *elabel, int32_t directed, Built &g) {
+    if (!ctx) return SGE_ERR_ARG;
+    std::string err;
+    if (!build_graph(n, m, src, dst, vlabel, elabel, directed, g, err)) return fail(ctx, SGE_ERR_ARG, err);
+    return SGE_OK;
+}
+
+void serve_worker(sge_ctx *ctx);
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char *sge_version(void) { return "sge-gb300 1.0 (sm_103a)"; }
+
+sge_status sge_create(sge_ctx **out, int32_t device, void *cuda_stream) {
+    if (!out) return SGE_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return SGE_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SGE_ERR_CUDA;
+    sge_ctx *ctx = new (std::nothrow) sge_ctx();
+    if (!ctx) return SGE_ERR_OOM;
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return SGE_ERR_CUDA; }
+        ctx->own_stream = true;
+    }
+    if (cudaHostAlloc(reinterpret_cast<void **>(&ctx->cancel_host), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&ctx->cancel_dev), ctx->cancel_host, 0) != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return SGE_ERR_CUDA;
+    }
+    *ctx->cancel_host = 0;
+    *out = ctx;
+    return SGE_OK;
+}
+
+void sge_destroy(sge_ctx *ctx) {
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> g(ctx->smu);
+        ctx->sstop = true;
+    }
+    ctx->scv.notify_all();
+    for (std::thread &t : ctx->sworkers) t.join();
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->targets) kv.second->release();
+    for (auto &kv : ctx->patterns) kv.second->release();
+    ctx->ws.release();
+    if (ctx->cancel_host) cudaFreeHost(ctx->cancel_host);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                           const int32_t *vlabel, const int32_t *elabel, int32_t directed, int32_t *target_id) {
+    if (!ctx || !target_id) return SGE_ERR_ARG;
+    Built g;
+    sge_status rc = load_graph_common(ctx, n, m, src, dst, vlabel, elabel, directed, g);
+    if (rc != SGE_OK) return rc;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    auto T = std::make_unique<TargetRec>();
+    T->n = n;
+    T->directed = g.directed;
+    T->any_elab = g.any_elab;
+    T->nnz = (long long)g.out.col.size();
+    T->dw = std::max(1, (n + 63) / 64);
+    std::vector<int2> vld((size_t)n);
+    for (int v = 0; v < n; ++v) vld[v] = make_int2(g.vlab[v], g.odeg[v]);
+    CK(upload(T->rowptr, g.out.ptr, st), "upload rowptr");
+    CK(upload(T->col, g.out.col, st), "upload col");
+    CK(upload(T->elab, g.out.lab, st), "upload elab");
+    CK(upload(T->vld, vld, st), "upload vertex info");
+    if (g.directed) {
+        CK(upload(T->irowptr, g.in.ptr, st), "upload in-rowptr");
+        CK(upload(T->icol, g.in.col, st), "upload in-col");
+        CK(upload(T->ielab, g.in.lab, st), "upload in-elab");
+        CK(upload(T->indeg, g.ideg, st), "upload in-degree");
+    } else if (n > 0 && n <= BITSET_MAX_N) {
+        std::vector<uint64_t> bits((size_t)n * T->dw, 0);
+        for (int v = 0; v < n; ++v)
+            for (int e = g.out.ptr[v]; e < g.out.ptr[v + 1]; ++e) {
+                const int w = g.out.col[e];
+                bits[(size_t)v * T->dw + (w >> 6)] |= 1ull << (w & 63);
+            }
+        CK(upload(T->adj, bits, st), "upload adjacency bitset");
+    }
+    CK(cudaStreamSynchronize(st), "target upload");
+    std::lock_guard<std::mutex> gd(ctx->mu);
+    const int id = ctx->next_target++;
+    ctx->targets[id] = std::move(T);
+    *target_id = id;
+    return SGE_OK;
+}
+
+sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                            const int32_t *vlabel, const int32_t *elabel, int32_t directed, int32_t *pattern_id) {
+    if (!ctx || !pattern_id) return SGE_ERR_ARG;
+    if (n > KMAX) return fail(ctx, SGE_ERR_ARG, "pattern has more than 128 vertices");
+    Built g;
+    sge_status rc = load_graph_common(ctx, n, m, src, dst, vlabel, elabel, directed, g);
+    if (rc != SGE_OK) return rc;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    auto P = std::make_unique<PatternRec>();
+    P->k = n;
+    P->directed = g.directed;
+    P->any_elab = g.any_elab;
+    P->lab = g.vlab;
+    P->odeg = g.odeg;
+    P->ideg = g.ideg;
+    P->amat.assign((size_t)n * n, NO_ARC);
+    P->nb.assign(n, std::vector<uint64_t>(2, 0));
+    for (int v = 0; v < n; ++v)
+        for (int e = g.out.ptr[v]; e < g.out.ptr[v + 1]; ++e) {
+            const int w = g.out.col[e];
+            P->amat[(size_t)v * n + w] = g.out.lab[e];
+            P->nb[v][w >> 6] |= 1ull << (w & 63);
+            P->nb[w][v >> 6] |= 1ull << (v & 63);
+        }
+    gcf_order(*P, SGE_RI, nullptr, P->ri_mu, P->ri_par);
+    CK(upload(P->dlab, g.vlab, st), "upload pattern labels");
+    CK(upload(P->dodeg, g.odeg, st), "upload pattern degrees");
+    CK(upload(P->drow, g.out.ptr, st), "upload pattern rows");
+    CK(upload(P->dcol, g.out.col, st), "upload pattern cols");
+    CK(upload(P->delab, g.out.lab, st), "upload pattern edge labels");
+    if (g.directed) {
+        CK(upload(P->dideg, g.ideg, st), "upload pattern in-degrees");
+        CK(upload(P->dirow, g.in.ptr, st), "upload pattern in-rows");
+        CK(upload(P->dicol, g.in.col, st), "upload pattern in-cols");
+        CK(upload(P->dielab, g.in.lab, st), "upload pattern in-labels");
+    }
+    CK(cudaStreamSynchronize(st), "pattern upload");
+    std::lock_guard<std::mutex> gd(ctx->mu);
+    const int id = ctx->next_pattern++;
+    ctx->patterns[id] = std::move(P);
+    *pattern_id = id;
+    return SGE_OK;
+}
+
+sge_status sge_unload_target(sge_ctx *ctx, int32_t target_id) {
+    if (!ctx) return SGE_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->targets.find(target_id);
+    if (it == ctx->targets.end()) return SGE_ERR_NOT_FOUND;
+    cudaStreamSynchronize(ctx->stream);
+    it->second->release();
+    ctx->targets.erase(it);
+    return SGE_OK;
+}
+
+sge_status sge_unload_pattern(sge_ctx *ctx, int32_t pattern_id) {
+    if (!ctx) return SGE_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->patterns.find(pattern_id);
+    if (it == ctx->patterns.end()) return SGE_ERR_NOT_FOUND;
+    cudaStreamSynchronize(ctx->stream);
+    it->second->release();
+    ctx->patterns.erase(it);
+    return SGE_OK;
+}
+
+sge_status sge_count(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts, sge_result *out) {
+    if (!ctx || !out) return SGE_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    *ctx->cancel_host = 0;
+    std::vector<PairReq> reqs{{target_id, pattern_id}};
+    return run_pairs(ctx, ctx->ws, ctx->stream, reqs, opts, out, false, nullptr, 0);
+}
+
+sge_status sge_count_batch(sge_ctx *ctx, int64_t npairs, const int32_t *target_ids, const int32_t *pattern_ids,
+                           const sge_opts *opts, sge_result *out) {
+    if (!ctx || !out || npairs < 0 || (npairs > 0 && (!target_ids || !pattern_ids))) return SGE_ERR_ARG;
+    if (npairs > INT32_MAX / 8) return fail(ctx, SGE_ERR_ARG, "too many pairs");
+    cudaSetDevice(ctx->device);
+    *ctx->cancel_host = 0;
+    std::vector<PairReq> reqs((size_t)npairs);
+    for (int64_t i = 0; i < npairs; ++i) reqs[i] = {target_ids[i], pattern_ids[i]};
+    if (npairs == 0) return SGE_OK;
+    return run_pairs(ctx, ctx->ws, ctx->stream, reqs, opts, out, false, nullptr, 0);
+}
+
+sge_status sge_enumerate(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts,
+                         sge_match_sink sink, void *user, sge_result *out) {
+    if (!ctx || !out || !sink) return SGE_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    *ctx->cancel_host = 0;
+    std::vector<PairReq> reqs{{target_id, pattern_id}};
+    // count first to size the match buffer exactly, then enumerate
+    sge_result first;
+    sge_status rc = run_pairs(ctx, ctx->ws, ctx->stream, reqs, opts, &first, false, nullptr, 0);
+    if (rc != SGE_OK) { *out = first; return rc; }
+    int k = 0;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        k = ctx->patterns.at(pattern_id)->k;
+    }
+    if ((long long)first.matches * std::max(k, 1) * 4 > (1ll << 32))
+        return fail(ctx, SGE_ERR_OOM, "match list larger than 4 GiB; use sge_count");
+    std::vector<int32_t> rows;
+    rc = run_pairs(ctx, ctx->ws, ctx->stream, reqs, opts, out, true, &rows, (long long)first.matches);
+    if (rc != SGE_OK) return rc;
+    const long long n = k > 0 ? (long long)rows.size() / k : 0;
+    const long long chunk = 1 << 16;
+    for (long long i = 0; i < n; i += chunk) {
+        const long long c = std::min(chunk, n - i);
+        if (sink(user, rows.data() + i * k, c, k) != 0) return fail(ctx, SGE_ERR_STOPPED, "sink stopped");
+    }
+    return SGE_OK;
+}
+
+sge_status sge_cancel(sge_ctx *ctx) {
+    if (!ctx || !ctx->cancel_host) return SGE_ERR_ARG;
+    *reinterpret_cast<volatile int *>(ctx->cancel_host) = 1;
+    return SGE_OK;
+}
+
+const char *sge_last_error(sge_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"
+
+// ================================================================ serving
+
+namespace {
+
+constexpr int SERVE_SLOTS = 4;               // concurrent launch groups (one stream each)
+constexpr int SERVE_GROUP_MAX = 64;          // queries admitted into one launch
+constexpr long long SERVE_BYTES = 2ll << 30; // device memory budget for admitted queries
+
+long long query_bytes(const TargetRec &t, const PatternRec &p) {
+    // filter block + frontier estimate + pool share
+    return (long long)p.k * t.dw * 8 + (1ll << 20);
+}
+
+void serve_worker(sge_ctx *ctx) {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    Workspace W;
+    for (;;) {
+        std::vector<std::shared_ptr<ServeReq>> group;
+        long long bytes = 0;
+        {
+            std::unique_lock<std::mutex> lk(ctx->smu);
+            ctx->scv.wait(lk, [&] { return ctx->sstop || !ctx->squeue.empty(); });
+            if (ctx->sstop && ctx->squeue.empty()) break;
+            // admit queued queries while they fit the memory budget
+            while (!ctx->squeue.empty() && (int)group.size() < SERVE_GROUP_MAX) {
+                auto &r = ctx->squeue.front();
+                if (!group.empty() && (ctx->sbytes_in_use + bytes + r->bytes > SERVE_BYTES ||
+                                       std::memcmp(&r->opts, &group[0]->opts, sizeof(sge_opts)) != 0))
+                    break;
+                bytes += r->bytes;
+                group.push_back(r);
+                ctx->squeue.pop_front();
+            }
+            ctx->sbytes_in_use += bytes;
+            ctx->sinflight += (int)group.size();
+        }
+        std::vector<PairReq> reqs;
+        for (auto &r : group) reqs.push_back({r->tid, r->pid});
+        std::vector<sge_result> res(group.size());
+        sge_status rc = run_pairs(ctx, W, st, reqs, &group[0]->opts, res.data(), false, nullptr, 0);
+        {
+            std::lock_guard<std::mutex> lk(ctx->smu);
+            for (size_t i = 0; i < group.size(); ++i) {
+                group[i]->res = res[i];
+                if (rc != SGE_OK && res[i].status == 0) group[i]->res.status = rc;
+                group[i]->done = true;
+            }
+            ctx->sbytes_in_use -= bytes;
+            ctx->sinflight -= (int)group.size();
+        }
+        ctx->scv.notify_all();
+    }
+    W.release();
+    cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+sge_status sge_serve_submit(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts,
+                            int64_t *ticket) {
+    if (!ctx || !ticket) return SGE_ERR_ARG;
+    auto r = std::make_shared<ServeReq>();
+    r->tid = target_id;
+    r->pid = pattern_id;
+    std::memset(&r->opts, 0, sizeof(sge_opts));
+    if (opts) r->opts = *opts;
+    std::memset(&r->res, 0, sizeof(r->res));
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto ti = ctx->targets.find(target_id);
+        auto pi = ctx->patterns.find(pattern_id);
+        if (ti == ctx->targets.end() || pi == ctx->patterns.end()) {
+            ctx->err = "unknown target or pattern id";
+            return SGE_ERR_NOT_FOUND;
+        }
+        r->bytes = query_bytes(*ti->second, *pi->second);
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        if (ctx->sworkers.empty())
+            for (int i = 0; i < SERVE_SLOTS; ++i) ctx->sworkers.emplace_back(serve_worker, ctx);
+        *ticket = ctx->next_ticket++;
+        ctx->sreqs[*ticket] = r;
+        ctx->squeue.push_back(r);
+    }
+    ctx->scv.notify_all();
+    return SGE_OK;
+}
+
+sge_status sge_serve_poll(sge_ctx *ctx, int64_t ticket, int32_t *done, sge_result *out) {
+    if (!ctx || !done) return SGE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    auto it = ctx->sreqs.find(ticket);
+    if (it == ctx->sreqs.end()) return SGE_ERR_NOT_FOUND;
+    *done = it->second->done ? 1 : 0;
+    if (*done) {
+        if (out) *out = it->second->res;
+        ctx->sreqs.erase(it);
+    }
+    return SGE_OK;
+}
+
+sge_status sge_serve_drain(sge_ctx *ctx) {
+    if (!ctx) return SGE_ERR_ARG;
+    std::unique_lock<std::mutex> lk(ctx->smu);
+    ctx->scv.wait(lk, [&] { return ctx->squeue.empty() && ctx->sinflight == 0; });
+    return SGE_OK;
+}
+
+}  // extern "C"

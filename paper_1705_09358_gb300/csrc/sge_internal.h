@@ -1,0 +1,156 @@
+// sge_internal.h -- device-side tables shared by the host and kernel units.
+//
+// Layout in HBM (all owned by the context):
+//   target:  CSR rows sorted ascending (int32 offsets `rowptr[n+1]`, int32
+//            neighbours `col`, int32 edge labels `elab`), `vld[n]` = {label,
+//            out-degree} as one 8-byte gather, in-rows for directed graphs,
+//            and for small undirected targets an n x dw adjacency bitset
+//            (dw = ceil(n / 64) 64-bit words per row).
+//   pattern: vertex-indexed label / degree arrays and CSR rows (used by the
+//            domain kernels), plus per-search "position tables" (PosInfo,
+//            BackEdge) built on the host from the ordering.
+//   filter:  per (job, pattern vertex) a dw-word bitset over target vertices:
+//            the RI-DS domain D(v) (Section 4) or, for RI, the label/degree
+//            filter of rules 2-3.
+//   frames:  int32 records [job, depth, begin, end, M_0 .. M_{depth-1}].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sge {
+
+constexpr int KMAX = 128;            // largest pattern handled by the kernels
+constexpr int FRAME_HDR = 4;         // job, depth, begin, end
+constexpr int POOL_STRIDE = FRAME_HDR + KMAX;
+
+// PosInfo.flags
+constexpr int POS_IN_ROW = 1;        // candidates come from the parent's in-row (directed)
+
+// JobDesc.flags
+constexpr int JOB_RIDS = 1;          // test v_t in D(mu_i) for every candidate
+constexpr int JOB_ELAB = 2;          // compare edge labels
+constexpr int JOB_DIRECTED = 4;
+constexpr int JOB_FC = 8;            // forward checking of singleton domains
+
+// One search position i of a job: pattern vertex mu_i and its constraints.
+struct PosInfo {
+    int32_t pv;     // mu_i
+    int32_t par;    // position of P(mu_i), or -1 when unparented
+    int32_t lab;    // lab(mu_i)
+    int32_t odeg;   // out-degree of mu_i (undirected: degree)
+    int32_t ideg;   // in-degree of mu_i (directed)
+    int32_t pel;    // label of the pattern arc joining mu_i and P(mu_i) along the row used
+    int32_t bbeg;   // back edges [bbeg, bbeg + bcnt) in the job's BackEdge array
+    int32_t bcnt;
+    int32_t ucnt;   // unparented: number of raw candidates (n_t for RI, |D(mu_i)| for RI-DS)
+    int32_t uoff;   // unparented RI-DS: offset of D(mu_i) in the job's candidate list
+    int32_t flags;  // POS_IN_ROW
+    int32_t pad;
+};
+
+// A pattern edge from mu_i back to an earlier position j (rule 4).
+struct BackEdge {
+    int32_t pos;      // j
+    int32_t dir;      // bit 0: arc mu_i -> mu_j needed; bit 1: arc mu_j -> mu_i needed
+    int32_t lab_out;  // label of mu_i -> mu_j (undirected: the edge label)
+    int32_t lab_in;   // label of mu_j -> mu_i
+};
+
+struct TargetView {
+    int32_t n;
+    int32_t dw;                 // 64-bit words per bitset row
+    const int32_t *rowptr;      // out-rows (undirected: all neighbours)
+    const int32_t *col;
+    const int32_t *elab;
+    const int32_t *irowptr;     // in-rows (directed)
+    const int32_t *icol;
+    const int32_t *ielab;
+    const int2 *vld;            // {label, out-degree}
+    const int32_t *indeg;       // directed
+    const uint64_t *adj;        // adjacency bitset rows (undirected, small n) or null
+};
+
+struct PatternView {
+    int32_t k;
+    int32_t pad;
+    const int32_t *lab;         // vertex-indexed
+    const int32_t *odeg;
+    const int32_t *ideg;
+    const int32_t *rowptr;      // out-rows (undirected: all neighbours)
+    const int32_t *col;
+    const int32_t *elab;
+    const int32_t *irowptr;     // in-rows (directed)
+    const int32_t *icol;
+    const int32_t *ielab;
+};
+
+struct JobDesc {
+    TargetView t;
+    PatternView p;
+    const PosInfo *pos;
+    const BackEdge *back;
+    uint64_t *filt;             // k x t.dw words: D(v) / label-degree filter, or null
+    const int32_t *ulist;       // candidate lists of unparented RI-DS positions
+    int32_t k;
+    int32_t flags;
+    unsigned long long *ctr;    // [4]: matches, states, nodes, hash
+    int32_t *mbuf;              // enumerate: match rows (k ints each), or null
+    long long mcap;             // rows that fit in mbuf
+    unsigned long long *mlen;   // rows produced (may exceed mcap)
+    unsigned long long *abytes; // algorithmic bytes of the bitset search
+};
+
+// Control block of one persistent search launch.
+struct SearchCtl {
+    const int32_t *front;       // frontier frames, stride fstride
+    long long nfront;           // frames of this shard
+    int32_t fstride;
+    int32_t shard_index, shard_count;
+    int32_t pcap;               // pool cells
+    unsigned long long *fnext;  // next frontier index (atomic)
+    int32_t *pool;              // pcap x POOL_STRIDE ints
+    unsigned long long *pseq;   // per-cell sequence numbers (bounded MPMC queue)
+    unsigned long long *phead, *ptail;
+    int *outstanding;           // frames not yet finished
+    int *idle;                  // warps waiting for work
+    int *status;                // first error code (0 = ok)
+    unsigned long long *donations;
+    const volatile int *cancel; // host-mapped cancel word (nonzero = stop), or null
+    unsigned long long deadline_ns;  // time limit in ns from each warp's start (%globaltimer), 0 = none
+    long long budget;           // states budget per job, 0 = none
+    int32_t donate;             // work donation on/off
+    int32_t gran;               // most frames per donation
+};
+
+// ------------------------------------------------------------ launchers
+// (implemented in sge_kernels.cu; all launch on `st`)
+
+cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
+                               long long nunits, cudaStream_t st);
+cudaError_t launch_domain_ac(const JobDesc *jobs, const long long *unit_off, int njobs,
+                             long long nunits, int *changed, cudaStream_t st);
+cudaError_t launch_domain_fc(const JobDesc *jobs, int njobs, int *changed, cudaStream_t st);
+cudaError_t launch_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
+                                long long nverts, long long *sizes, cudaStream_t st);
+cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert,
+                                const int *task_out, int ntasks, int32_t *lists, cudaStream_t st);
+
+// BFS split of one level: pass 0 counts children per frame, pass 1 writes
+// them at `offs` and accumulates the level's counters into the jobs.
+cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, int depth,
+                         int32_t *counts, const long long *offs, int32_t *fout, int pass,
+                         int count_ctr, int directed, cudaStream_t st);
+cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,
+                        void *tmp, size_t tmp_bytes, cudaStream_t st);
+size_t scan_tmp_bytes(long long n);
+
+// Persistent search.  kernel: 1 = CSR, 2 = bitset.  Returns the grid size used.
+cudaError_t launch_search(int kernel, const JobDesc *jobs, const SearchCtl &ctl, int kmax, int nwl,
+                          int directed, int blocks_per_sm, int *grid_out, cudaStream_t st);
+int search_warps_per_block();
+cudaError_t search_blocks_per_sm(int kernel, int kmax, int nwl, int directed, int *occ);
+cudaError_t launch_pool_init(unsigned long long *seq, int cap, cudaStream_t st);
+size_t search_smem_bytes(int kernel, int kmax, int nwl);
+
+}  // namespace sge

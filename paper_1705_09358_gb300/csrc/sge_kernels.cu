@@ -1,0 +1,1161 @@
+// sge_kernels.cu -- sm_103a kernels of the subgraph-enumeration engine.
+//
+// Method (arXiv 1705.09358): RI backtracking search (Section "RI": static
+// GreatestConstraintFirst order, candidates from the adjacency of the
+// parent's image, pruning rules 1-4) and RI-DS (Section 4: domains D(v)
+// pruned by arc consistency, forward checking of singleton domains).
+//
+// GPU design (not the paper's CPU work-stealing runtime):
+//  * domain kernels: one warp per 64-target bitset word; arc consistency and
+//    forward checking iterate to their joint fixpoint under a host loop;
+//  * split: breadth-first expansion of the search tree, one warp per frame,
+//    until the frontier holds enough frames for every resident warp;
+//  * persistent search: one warp owns one depth-first search.  The CSR kernel
+//    scans the candidate row 32 candidates at a time (one per lane), tests
+//    rules 1-4 per lane and compacts survivors with a ballot; the bitset kernel
+//    computes a whole candidate set as the AND of the parent's adjacency row,
+//    the back-neighbours' rows and the filter D(mu_i), one 64-bit word per
+//    lane.  Idle warps take frames from the frontier, then from a bounded
+//    lock-free queue into which busy warps donate their shallowest unexplored
+//    work (the paper's "steal from the back of the deque" idea without deques).
+//  * every wait is bounded; cancellation, deadline and state budget are
+//    checked periodically and reported through a status word.
+#include "sge_internal.h"
+
+#include <cuda/atomic>
+
+namespace sge {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARPS_PER_BLOCK = 8;
+constexpr int BLOCK = WARPS_PER_BLOCK * 32;
+constexpr int CHECK_EVERY = 64;          // iterations between donation / abort checks
+constexpr long long IDLE_SPIN_LIMIT = 1ll << 31;
+constexpr int QUEUE_ATTEMPTS = 64;
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// g(u, v) of the per-match hash h(f) = fmix64(sum_u g(u, f(u))).
+__device__ __forceinline__ uint64_t gterm(int u, int v) {
+    return fmix64(((uint64_t)(uint32_t)u << 32 | (uint64_t)(uint32_t)v) + 0x9E3779B97F4A7C15ull);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long load_acquire(unsigned long long *p) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
+    return r.load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void store_release(unsigned long long *p, unsigned long long v) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
+    r.store(v, cuda::memory_order_release);
+}
+__device__ __forceinline__ int load_relaxed(int *p) {
+    cuda::atomic_ref<int, cuda::thread_scope_device> r(*p);
+    return r.load(cuda::memory_order_relaxed);
+}
+
+__device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
+
+// Is `c` in the sorted row of `x` (with edge label `lab` when `chk`)?
+__device__ __forceinline__ bool row_has(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                        const int32_t *__restrict__ elab, int x, int c, int lab, bool chk) {
+    int lo = __ldg(rowptr + x), hi = __ldg(rowptr + x + 1);
+    const int end = hi;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(col + mid) < c) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= end || __ldg(col + lo) != c) return false;
+    return !chk || __ldg(elab + lo) == lab;
+}
+
+// Candidate source of position i (Section "RI": neighbours of M(P(mu_i));
+// all of V_t, or D(mu_i) for RI-DS, when mu_i has no parent).
+struct Src {
+    const int32_t *ptr;   // null: candidate j is vertex j
+    long long base;
+    int len;
+};
+
+__device__ __forceinline__ Src cand_source(const JobDesc &J, const PosInfo &P, const int *M) {
+    Src s;
+    if (P.par >= 0) {
+        int a = M[P.par];
+        if (P.flags & POS_IN_ROW) {
+            int b = __ldg(J.t.irowptr + a);
+            s.ptr = J.t.icol; s.base = b; s.len = __ldg(J.t.irowptr + a + 1) - b;
+        } else {
+            int b = __ldg(J.t.rowptr + a);
+            s.ptr = J.t.col; s.base = b; s.len = __ldg(J.t.rowptr + a + 1) - b;
+        }
+    } else if (J.flags & JOB_RIDS) {
+        s.ptr = J.ulist; s.base = P.uoff; s.len = P.ucnt;
+    } else {
+        s.ptr = nullptr; s.base = 0; s.len = J.t.n;
+    }
+    return s;
+}
+
+// Rules 1-4 (Section "RI", pruning rules) and the RI-DS domain test for
+// mapping mu_i onto candidate c.  `eidx` is c's index in the parent's row
+// (for the parent-arc label), or -1.  M holds the images of positions 0..i-1.
+template <bool DIR>
+__device__ __forceinline__ bool feasible(const JobDesc &J, const PosInfo &P, int i, int c, long long eidx,
+                                         const int *M) {
+    const int2 v = __ldg(J.t.vld + c);
+    if (v.x != P.lab || v.y < P.odeg) return false;                       // rules 2, 3
+    if (DIR && __ldg(J.t.indeg + c) < P.ideg) return false;              // rule 3 (in)
+    if (J.flags & JOB_RIDS) {                                             // v_t in D(mu_i)
+        const uint64_t w = J.filt[(size_t)P.pv * J.t.dw + (c >> 6)];
+        if (!((w >> (c & 63)) & 1ull)) return false;
+    }
+    const bool chk = (J.flags & JOB_ELAB) != 0;
+    if (chk && eidx >= 0) {                                               // parent arc label
+        const int l = (P.flags & POS_IN_ROW) ? __ldg(J.t.ielab + eidx) : __ldg(J.t.elab + eidx);
+        if (l != P.pel) return false;
+    }
+    for (int b = 0; b < P.bcnt; ++b) {                                    // rule 4
+        const BackEdge be = J.back[P.bbeg + b];
+        const int x = M[be.pos];
+        if (!DIR) {
+            if (J.t.adj != nullptr && !chk) {
+                const uint64_t w = __ldg(J.t.adj + (size_t)x * J.t.dw + (c >> 6));
+                if (!((w >> (c & 63)) & 1ull)) return false;
+            } else if (!row_has(J.t.rowptr, J.t.col, J.t.elab, x, c, be.lab_out, chk)) {
+                return false;
+            }
+        } else {
+            // arc c -> x: c is in the in-row of x; arc x -> c: c is in the out-row of x
+            if ((be.dir & 1) && !row_has(J.t.irowptr, J.t.icol, J.t.ielab, x, c, be.lab_out, chk)) return false;
+            if ((be.dir & 2) && !row_has(J.t.rowptr, J.t.col, J.t.elab, x, c, be.lab_in, chk)) return false;
+        }
+    }
+    for (int j = 0; j < i; ++j)                                           // rule 1
+        if (M[j] == c) return false;
+    return true;
+}
+
+__device__ __forceinline__ int find_job(const long long *off, int njobs, long long u) {
+    int lo = 0, hi = njobs;  // largest j with off[j] <= u
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Write one match row (images of pattern vertices 0..k-1) for enumeration.
+__device__ __forceinline__ void emit_match(const JobDesc &J, const int *M, int last_pos, int c) {
+    unsigned long long slot = atomicAdd(J.mlen, 1ull);
+    if ((long long)slot >= J.mcap) return;
+    int32_t *row = J.mbuf + (size_t)slot * J.k;
+    for (int t = 0; t < last_pos; ++t) row[J.pos[t].pv] = M[t];
+    row[J.pos[last_pos].pv] = c;
+}
+
+// ================================================================ domains
+
+// D(v) initialisation (Section 4): equal label, in/out-degree at least v's.
+// For RI it is exactly the rule 2-3 filter.  One warp per 64-bit word.
+__global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
+                                                       long long nunits) {
+    const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= nunits) return;
+    const int j = find_job(unit_off, njobs, u);
+    const JobDesc &J = jobs[j];
+    if (J.filt == nullptr) return;
+    const bool DIR = (J.flags & JOB_DIRECTED) != 0;
+    const long long local = u - unit_off[j];
+    const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
+    const int lab = J.p.lab[v], od = J.p.odeg[v], id = DIR ? J.p.ideg[v] : 0;
+    unsigned long long word = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int t = q * 64 + h * 32 + lane;
+        bool ok = false;
+        if (t < J.t.n) {
+            const int2 x = __ldg(J.t.vld + t);
+            ok = x.x == lab && x.y >= od && (!DIR || __ldg(J.t.indeg + t) >= id);
+        }
+        word |= (unsigned long long)__ballot_sync(FULL, ok) << (32 * h);
+    }
+    if (lane == 0) J.filt[(size_t)v * J.t.dw + q] = word;
+}
+
+// One arc-consistency sweep (Section 4): drop t from D(v) when a pattern
+// edge at v has no compatible target edge at t into the other endpoint's
+// domain.  Removals are applied in place (monotone), so sweeping until no
+// word changes reaches the unique greatest fixpoint.
+__global__ void __launch_bounds__(BLOCK) k_domain_ac(const JobDesc *jobs, const long long *unit_off, int njobs,
+                                                     long long nunits, int *changed) {
+    const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= nunits) return;
+    const int j = find_job(unit_off, njobs, u);
+    const JobDesc &J = jobs[j];
+    if (J.filt == nullptr || !(J.flags & JOB_RIDS)) return;
+    const bool DIR = (J.flags & JOB_DIRECTED) != 0;
+    const long long local = u - unit_off[j];
+    const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
+    uint64_t *wp = J.filt + (size_t)v * J.t.dw + q;
+    const uint64_t word = *wp;
+    if (word == 0) return;
+    const bool chk = (J.flags & JOB_ELAB) != 0;
+    const int dw = J.t.dw;
+    unsigned long long keep = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int bit = h * 32 + lane;
+        const int t = q * 64 + bit;
+        bool ok = (word >> bit) & 1ull;
+        if (ok) {
+            for (int e = J.p.rowptr[v]; ok && e < J.p.rowptr[v + 1]; ++e) {
+                const int uu = J.p.col[e], bl = chk ? J.p.elab[e] : 0;
+                const uint64_t *Du = J.filt + (size_t)uu * dw;
+                bool found = false;
+                for (int f = __ldg(J.t.rowptr + t), fe = __ldg(J.t.rowptr + t + 1); f < fe; ++f) {
+                    const int y = __ldg(J.t.col + f);
+                    if ((!chk || __ldg(J.t.elab + f) == bl) && ((Du[y >> 6] >> (y & 63)) & 1ull)) { found = true; break; }
+                }
+                ok = found;
+            }
+            if (DIR) {
+                for (int e = J.p.irowptr[v]; ok && e < J.p.irowptr[v + 1]; ++e) {
+                    const int uu = J.p.icol[e], bl = chk ? J.p.ielab[e] : 0;
+                    const uint64_t *Du = J.filt + (size_t)uu * dw;
+                    bool found = false;
+                    for (int f = __ldg(J.t.irowptr + t), fe = __ldg(J.t.irowptr + t + 1); f < fe; ++f) {
+                        const int y = __ldg(J.t.icol + f);
+                        if ((!chk || __ldg(J.t.ielab + f) == bl) && ((Du[y >> 6] >> (y & 63)) & 1ull)) { found = true; break; }
+                    }
+                    ok = found;
+                }
+            }
+        }
+        keep |= (unsigned long long)__ballot_sync(FULL, ok) << (32 * h);
+    }
+    if (lane == 0 && keep != word) {
+        atomicAnd((unsigned long long *)wp, keep);
+        *changed = 1;
+    }
+}
+
+// Forward checking (Section 4.2): the target node of a singleton domain is
+// removed from every other domain, repeated until no singleton removes
+// anything.  One block per job.
+__global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, int *changed) {
+    __shared__ int cnt[KMAX];
+    __shared__ int elem[KMAX];
+    __shared__ int sing_t[KMAX];
+    __shared__ int sing_u[KMAX];
+    __shared__ int nsing;
+    __shared__ int any;
+    const JobDesc &J = jobs[blockIdx.x];
+    if (J.filt == nullptr || !(J.flags & JOB_FC)) return;
+    const int k = J.k, dw = J.t.dw;
+    const long long words = (long long)k * dw;
+    for (int round = 0; round < 4 * KMAX + 8; ++round) {
+        for (int v = threadIdx.x; v < k; v += blockDim.x) { cnt[v] = 0; elem[v] = -1; }
+        if (threadIdx.x == 0) { nsing = 0; any = 0; }
+        __syncthreads();
+        for (long long x = threadIdx.x; x < words; x += blockDim.x) {
+            const uint64_t w = J.filt[x];
+            if (w) {
+                const int v = (int)(x / dw), q = (int)(x % dw);
+                atomicAdd(&cnt[v], __popcll(w));
+                elem[v] = q * 64 + __ffsll((long long)w) - 1;
+            }
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < k; v += blockDim.x)
+            if (cnt[v] == 1) {
+                const int s = atomicAdd(&nsing, 1);
+                sing_u[s] = v;
+                sing_t[s] = elem[v];
+            }
+        __syncthreads();
+        const int ns = nsing;
+        if (ns == 0) break;
+        for (long long x = threadIdx.x; x < words; x += blockDim.x) {
+            const int v = (int)(x / dw), q = (int)(x % dw);
+            uint64_t mask = 0;
+            for (int s = 0; s < ns; ++s)
+                if (sing_u[s] != v && (sing_t[s] >> 6) == q) mask |= 1ull << (sing_t[s] & 63);
+            const uint64_t w = J.filt[x];
+            if (w & mask) { J.filt[x] = w & ~mask; any = 1; }
+        }
+        __syncthreads();
+        if (!any) break;
+        if (threadIdx.x == 0) *changed = 1;
+        __syncthreads();
+    }
+}
+
+// |D(v)| for every (job, pattern vertex); one warp each.
+__global__ void __launch_bounds__(BLOCK) k_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
+                                                        long long nverts, long long *sizes) {
+    const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= nverts) return;
+    const int j = find_job(vert_off, njobs, u);
+    const JobDesc &J = jobs[j];
+    const int v = (int)(u - vert_off[j]);
+    unsigned long long c = 0;
+    for (int q = lane; q < J.t.dw; q += 32) c += __popcll(J.filt[(size_t)v * J.t.dw + q]);
+    c = warp_sum(c);
+    if (lane == 0) sizes[u] = (long long)c;
+}
+
+// List D(v) in ascending id order at `out` (one block per task).
+__global__ void __launch_bounds__(BLOCK) k_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert,
+                                                        const int *task_out, int32_t *lists) {
+    __shared__ int wsum[WARPS_PER_BLOCK];
+    __shared__ int carry;
+    const JobDesc &J = jobs[task_job[blockIdx.x]];
+    const int v = task_vert[blockIdx.x];
+    int32_t *out = lists + task_out[blockIdx.x];
+    const uint64_t *row = J.filt + (size_t)v * J.t.dw;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < J.t.dw; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        const uint64_t word = q < J.t.dw ? row[q] : 0;
+        const int c = __popcll(word);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int before = carry;
+        for (int i = 0; i < w; ++i) before += wsum[i];
+        int pos = before + incl - c;
+        uint64_t x = word;
+        while (x) {
+            const int b = __ffsll((long long)x) - 1;
+            out[pos++] = q * 64 + b;
+            x &= x - 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int i = 0; i < WARPS_PER_BLOCK; ++i) tot += wsum[i];
+            carry += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// ================================================================== split
+
+// One level of the breadth-first split.  Each frame [job, depth, -1, -1, M]
+// is a search node whose positions 0..depth-1 are assigned; its candidates
+// for position `depth` are tested, and in pass 1 each survivor becomes a
+// frame of depth + 1 (or, at the last position, a match).
+template <bool DIR>
+__global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int32_t *fin, long long nf, int depth,
+                                                 int32_t *counts, const long long *offs, int32_t *fout, int pass,
+                                                 int count_ctr) {
+    __shared__ int Msh[WARPS_PER_BLOCK][KMAX];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *M = Msh[wib];
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int in_stride = FRAME_HDR + depth, out_stride = FRAME_HDR + depth + 1;
+    for (long long f = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nf; f += nwarps) {
+        const int32_t *fr = fin + f * in_stride;
+        const int j = fr[0];
+        const JobDesc &J = jobs[j];
+        for (int t = lane; t < depth; t += 32) M[t] = fr[FRAME_HDR + t];
+        __syncwarp();
+        const int k = J.k;
+        const bool leaf = depth + 1 == k;
+        const PosInfo P = J.pos[depth];
+        const Src S = cand_source(J, P, M);
+        unsigned long long psum = 0;
+        if (pass == 1 && leaf) {
+            for (int t = lane; t < depth; t += 32) psum += gterm(J.pos[t].pv, M[t]);
+            psum = warp_sum(psum);
+        }
+        const long long obase = (pass == 1 && !leaf) ? offs[f] : 0;
+        long long child = 0;
+        unsigned long long nodes = 0, hs = 0;
+        for (int c0 = 0; c0 < S.len; c0 += 32) {
+            const int idx = c0 + lane;
+            bool ok = false;
+            int c = -1;
+            if (idx < S.len) {
+                c = S.ptr ? __ldg(S.ptr + S.base + idx) : idx;
+                ok = feasible<DIR>(J, P, depth, c, (S.ptr && P.par >= 0) ? S.base + idx : -1, M);
+            }
+            const unsigned bal = __ballot_sync(FULL, ok);
+            const int cnt = __popc(bal);
+            if (pass == 1) {
+                nodes += cnt;
+                if (leaf) {
+                    if (ok && count_ctr) {
+                        hs += fmix64(psum + gterm(P.pv, c));
+                        if (J.mbuf) emit_match(J, M, depth, c);
+                    }
+                } else if (ok) {
+                    const long long o = obase + child + __popc(bal & ((1u << lane) - 1u));
+                    int32_t *dst = fout + o * out_stride;
+                    dst[0] = j; dst[1] = depth + 1; dst[2] = -1; dst[3] = -1;
+                    for (int t = 0; t < depth; ++t) dst[FRAME_HDR + t] = M[t];
+                    dst[FRAME_HDR + depth] = c;
+                }
+            }
+            child += cnt;
+        }
+        if (pass == 0) {
+            if (lane == 0) counts[f] = leaf ? 0 : (int32_t)child;
+        } else if (count_ctr) {
+            hs = warp_sum(hs);
+            if (lane == 0) {
+                atomicAdd(J.ctr + 1, (unsigned long long)S.len);
+                atomicAdd(J.ctr + 2, nodes);
+                if (leaf) {
+                    atomicAdd(J.ctr + 0, nodes);
+                    atomicAdd(J.ctr + 3, hs);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// =================================================================== scan
+
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = BLOCK * SCAN_ITEMS;
+
+__device__ __forceinline__ long long block_excl_scan(long long x, long long *total) {
+    __shared__ long long ws[WARPS_PER_BLOCK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    long long before = 0, tot = 0;
+    for (int i = 0; i < WARPS_PER_BLOCK; ++i) {
+        if (i < w) before += ws[i];
+        tot += ws[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return before + incl - x;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_scan_tiles(const int32_t *in, long long *out, long long n, long long *tile_sum) {
+    const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    long long v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    long long tot;
+    long long ex = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_scan_sums(long long *tile_sum, long long ntiles, long long *total) {
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b = 0; b < ntiles; b += BLOCK) {
+        const long long i = b + threadIdx.x;
+        const long long x = i < ntiles ? tile_sum[i] : 0;
+        long long tot;
+        const long long ex = block_excl_scan(x, &tot);
+        if (i < ntiles) tile_sum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_scan_add(long long *out, long long n, const long long *tile_sum) {
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
+    const long long add = tile_sum[blockIdx.x];
+    for (int i = threadIdx.x; i < SCAN_TILE; i += BLOCK)
+        if (base + i < n) out[base + i] += add;
+}
+
+// ========================================================= frame queue
+
+// Bounded multi-producer multi-consumer queue with per-cell sequence numbers
+// (cell c starts at seq c; a producer owns ticket t when seq == t, a consumer
+// when seq == t + 1).  Lane 0 only.  Neither call waits: each returns -1 when
+// the queue is full / empty or after QUEUE_ATTEMPTS contended tries.
+__device__ long long queue_reserve(const SearchCtl &C) {
+    unsigned long long pos = load_acquire(C.ptail);
+    for (int a = 0; a < QUEUE_ATTEMPTS; ++a) {
+        const unsigned long long seq = load_acquire(C.pseq + (pos % (unsigned long long)C.pcap));
+        const long long dif = (long long)(seq - pos);
+        if (dif == 0) {
+            if (atomicCAS(C.ptail, pos, pos + 1) == pos) return (long long)pos;
+            pos = load_acquire(C.ptail);
+        } else if (dif < 0) {
+            return -1;
+        } else {
+            pos = load_acquire(C.ptail);
+        }
+    }
+    return -1;
+}
+
+__device__ long long queue_claim(const SearchCtl &C) {
+    unsigned long long pos = load_acquire(C.phead);
+    for (int a = 0; a < QUEUE_ATTEMPTS; ++a) {
+        const unsigned long long seq = load_acquire(C.pseq + (pos % (unsigned long long)C.pcap));
+        const long long dif = (long long)(seq - (pos + 1));
+        if (dif == 0) {
+            if (atomicCAS(C.phead, pos, pos + 1) == pos) return (long long)pos;
+            pos = load_acquire(C.phead);
+        } else if (dif < 0) {
+            return -1;
+        } else {
+            pos = load_acquire(C.phead);
+        }
+    }
+    return -1;
+}
+
+// Warp-collective: push frame [j, depth, beg, end, M[0..mlen-1] (+ last)]
+// (`last` >= 0 appends one more image).  Returns false if the queue is full.
+__device__ bool push_frame(const SearchCtl &C, int j, int depth, int beg, int end, const int *M, int mlen, int last) {
+    const int lane = threadIdx.x & 31;
+    long long t = -1;
+    if (lane == 0) {
+        atomicAdd(C.outstanding, 1);
+        t = queue_reserve(C);
+        if (t < 0) atomicSub(C.outstanding, 1);
+    }
+    t = __shfl_sync(FULL, t, 0);
+    if (t < 0) return false;
+    int32_t *cell = C.pool + (size_t)(t % C.pcap) * POOL_STRIDE;
+    if (lane == 0) { cell[0] = j; cell[1] = depth; cell[2] = beg; cell[3] = end; }
+    for (int i = lane; i < mlen; i += 32) cell[FRAME_HDR + i] = M[i];
+    if (last >= 0 && lane == 0) cell[FRAME_HDR + mlen] = last;
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        store_release(C.pseq + (t % C.pcap), (unsigned long long)t + 1);
+        atomicAdd(C.donations, 1ull);
+    }
+    __syncwarp();
+    return true;
+}
+
+struct Frame {
+    int job, depth, beg, end;
+};
+
+// Warp-collective: take the next frame (frontier first, then the queue) and
+// copy its images into M.  Waits (bounded) while other warps still hold work.
+// Returns false when the search is over or stopped.
+__device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned long long deadline) {
+    const int lane = threadIdx.x & 31;
+    bool idle = false;
+    long long spins = 0;
+    int kind = 0;        // 1 frontier, 2 queue, 0 stop
+    long long idx = -1;
+    for (;;) {
+        kind = -1;
+        if (lane == 0) {
+            if (load_relaxed(C.status) != 0) {
+                kind = 0;
+            } else {
+                if (load_acquire(C.fnext) < (unsigned long long)C.nfront) {
+                    const unsigned long long f = atomicAdd(C.fnext, 1ull);
+                    if ((long long)f < C.nfront) { kind = 1; idx = (long long)f; }
+                }
+                if (kind < 0) {
+                    const long long t = queue_claim(C);
+                    if (t >= 0) { kind = 2; idx = t; }
+                }
+                if (kind < 0 && load_relaxed(C.outstanding) == 0) kind = 0;
+            }
+            if (kind < 0) {
+                if (!idle) { atomicAdd(C.idle, 1); idle = true; }
+                if (++spins > IDLE_SPIN_LIMIT) { set_status(C.status, -5); kind = 0; }
+                else if ((spins & 1023) == 0) {
+                    if ((C.cancel != nullptr && *C.cancel != 0)) { set_status(C.status, -6); kind = 0; }
+                    else if (deadline != 0 && globaltimer() > deadline) { set_status(C.status, -5); kind = 0; }
+                }
+            }
+        }
+        kind = __shfl_sync(FULL, kind, 0);
+        if (kind >= 0) break;
+        __nanosleep(200);
+    }
+    if (lane == 0 && idle) atomicSub(C.idle, 1);
+    if (kind == 0) return false;
+    idx = __shfl_sync(FULL, idx, 0);
+    const int32_t *src;
+    if (kind == 1) {
+        const long long g = idx * (long long)C.shard_count + C.shard_index;
+        src = C.front + g * C.fstride;
+    } else {
+        if (lane == 0) __threadfence();
+        __syncwarp();
+        src = C.pool + (size_t)(idx % C.pcap) * POOL_STRIDE;
+    }
+    fr.job = src[0]; fr.depth = src[1]; fr.beg = src[2]; fr.end = src[3];
+    for (int i = lane; i < fr.depth; i += 32) M[i] = src[FRAME_HDR + i];
+    __syncwarp();
+    if (kind == 2 && lane == 0) {
+        __threadfence();
+        store_release(C.pseq + (idx % C.pcap), (unsigned long long)idx + C.pcap);
+    }
+    return true;
+}
+
+// Periodic checks by lane 0: cancellation, deadline, budget, other warps'
+// errors.  Returns nonzero (warp-uniform) when the warp must stop.
+__device__ __forceinline__ int must_stop(const SearchCtl &C, const JobDesc &J, unsigned long long local_states,
+                                         unsigned long long deadline) {
+    int stop = 0;
+    if ((threadIdx.x & 31) == 0) {
+        if (load_relaxed(C.status) != 0) stop = 1;
+        else if (C.cancel != nullptr && *C.cancel != 0) { set_status(C.status, -6); stop = 1; }
+        else if (deadline != 0 && globaltimer() > deadline) { set_status(C.status, -5); stop = 1; }
+        else if (C.budget > 0 && (long long)(*(volatile unsigned long long *)(J.ctr + 1) + local_states) > C.budget) {
+            set_status(C.status, -4); stop = 1;
+        }
+    }
+    return __shfl_sync(FULL, stop, 0);
+}
+
+__device__ __forceinline__ bool donation_wanted(const SearchCtl &C) {
+    int want = 0;
+    if ((threadIdx.x & 31) == 0 && C.donate) {
+        const int idle = load_relaxed(C.idle);
+        if (idle > 0) {
+            const long long occ = (long long)(load_acquire(C.ptail) - load_acquire(C.phead));
+            want = occ < idle && occ < C.pcap / 2;
+        }
+    }
+    return __shfl_sync(FULL, want, 0) != 0;
+}
+
+// ===================================================== search: CSR kernel
+
+struct LvCsr {
+    const int32_t *ptr;  // candidate array (null = identity)
+    long long base;      // offset of the candidate list in ptr
+    int cur, end;        // unscanned candidates [cur, end)
+    unsigned mask;       // survivors of the last scanned chunk, not yet descended
+    int cbase;           // index of that chunk's first candidate
+};
+
+__host__ __device__ __forceinline__ size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ __forceinline__ size_t csr_smem_per_warp(int kmax) {
+    return round16((size_t)(kmax + 1) * sizeof(unsigned long long) + (size_t)kmax * sizeof(LvCsr) +
+                   (size_t)kmax * sizeof(int));
+}
+
+template <bool DIR>
+__global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, SearchCtl C, int kmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *base = smem + wib * csr_smem_per_warp(kmax);
+    unsigned long long *psum = reinterpret_cast<unsigned long long *>(base);
+    LvCsr *lv = reinterpret_cast<LvCsr *>(psum + kmax + 1);
+    int *M = reinterpret_cast<int *>(lv + kmax);
+
+    // the time limit counts from this warp's start on the device clock
+    const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
+    Frame fr;
+    long long iter = 0;
+    while (acquire_frame(C, M, fr, deadline)) {
+        const JobDesc &J = jobs[fr.job];
+        const int k = J.k, d0 = fr.depth;
+        unsigned long long st = 0, nd = 0, mt = 0, hs = 0;
+        {
+            unsigned long long s = 0;
+            for (int t = lane; t < d0; t += 32) s += gterm(J.pos[t].pv, M[t]);
+            s = warp_sum(s);
+            if (lane == 0) psum[d0] = s;
+        }
+        {
+            const PosInfo P = J.pos[d0];
+            const Src S = cand_source(J, P, M);
+            int cur = 0, end = S.len;
+            if (fr.beg >= 0) { cur = fr.beg; end = min(fr.end, S.len); }
+            else st += (unsigned long long)S.len;
+            if (lane == 0) { lv[d0].ptr = S.ptr; lv[d0].base = S.base; lv[d0].cur = cur; lv[d0].end = end; lv[d0].mask = 0; lv[d0].cbase = 0; }
+            __syncwarp();
+        }
+        int lvl = d0;
+        bool stopped = false;
+        for (;;) {
+            if (((++iter) & (CHECK_EVERY - 1)) == 0) {
+                if (C.budget > 0) {
+                    if (lane == 0) atomicAdd(J.ctr + 1, st);
+                    st = 0;
+                }
+                if (must_stop(C, J, st, deadline)) { stopped = true; break; }
+                if (donation_wanted(C)) {
+                    // donate the shallowest unexplored work: half of an unscanned
+                    // range, else up to `gran` pending survivors as new search nodes
+                    for (int l = d0; l <= lvl; ++l) {
+                        LvCsr &L = lv[l];
+                        const int rem = L.end - L.cur;
+                        if (rem >= 64) {
+                            const int mid = L.cur + ((rem / 2 + 31) & ~31);
+                            if (push_frame(C, fr.job, l, mid, L.end, M, l, -1)) {
+                                __syncwarp();
+                                if (lane == 0) L.end = mid;
+                                __syncwarp();
+                            }
+                            break;
+                        }
+                        if (L.mask != 0) {
+                            int given = 0;
+                            while (L.mask != 0 && given < C.gran) {
+                                const unsigned m = L.mask;
+                                const int b = __ffs(m) - 1;
+                                const int c = L.ptr ? __ldg(L.ptr + L.base + L.cbase + b) : L.cbase + b;
+                                if (!push_frame(C, fr.job, l + 1, -1, -1, M, l, c)) break;
+                                __syncwarp();
+                                if (lane == 0) L.mask = m & (m - 1);
+                                __syncwarp();
+                                ++given;
+                            }
+                            break;
+                        }
+                    }
+                }
+            }
+            LvCsr &L = lv[lvl];
+            const unsigned mask = L.mask;
+            if (mask == 0) {
+                const int cur = L.cur, end = L.end;
+                if (cur >= end) {
+                    if (lvl == d0) break;
+                    --lvl;
+                    continue;
+                }
+                const int cnt = min(32, end - cur);
+                const PosInfo P = J.pos[lvl];
+                bool ok = false;
+                int c = -1;
+                if (lane < cnt) {
+                    const long long e = L.base + cur + lane;
+                    c = L.ptr ? __ldg(L.ptr + e) : cur + lane;
+                    ok = feasible<DIR>(J, P, lvl, c, (L.ptr && P.par >= 0) ? e : -1, M);
+                }
+                unsigned bal = __ballot_sync(FULL, ok);
+                nd += __popc(bal);
+                if (lvl == k - 1) {
+                    mt += __popc(bal);
+                    if (ok) {
+                        hs += fmix64(psum[lvl] + gterm(P.pv, c));
+                        if (J.mbuf) emit_match(J, M, lvl, c);
+                    }
+                    bal = 0;
+                }
+                __syncwarp();
+                if (lane == 0) { L.cur = cur + cnt; L.mask = bal; L.cbase = cur; }
+                __syncwarp();
+                continue;
+            }
+            // descend into the lowest pending survivor
+            const int b = __ffs(mask) - 1;
+            const int c = L.ptr ? __ldg(L.ptr + L.base + L.cbase + b) : L.cbase + b;
+            const int pv = J.pos[lvl].pv;
+            __syncwarp();
+            if (lane == 0) {
+                L.mask = mask & (mask - 1);
+                M[lvl] = c;
+                psum[lvl + 1] = psum[lvl] + gterm(pv, c);
+            }
+            __syncwarp();
+            ++lvl;
+            const PosInfo Q = J.pos[lvl];
+            const Src S = cand_source(J, Q, M);
+            st += (unsigned long long)S.len;
+            if (lane == 0) { lv[lvl].ptr = S.ptr; lv[lvl].base = S.base; lv[lvl].cur = 0; lv[lvl].end = S.len; lv[lvl].mask = 0; lv[lvl].cbase = 0; }
+            __syncwarp();
+        }
+        hs = warp_sum(hs);
+        if (lane == 0) {
+            atomicAdd(J.ctr + 0, mt);
+            atomicAdd(J.ctr + 1, st);
+            atomicAdd(J.ctr + 2, nd);
+            atomicAdd(J.ctr + 3, hs);
+            if (!stopped) atomicSub(C.outstanding, 1);
+        }
+        __syncwarp();
+        if (stopped) break;
+    }
+}
+
+// ================================================== search: bitset kernel
+//
+// Candidate set of position i as one AND over bitset rows (dense targets):
+//   S_i = D(mu_i) & A[M(P(mu_i))] & AND_j A[M(mu_j)] & ~{M_0..M_{i-1}}
+// where D is the domain (RI-DS) or the label/degree filter (RI) and A the
+// adjacency bitset.  Lane l owns words l, l + 32, ... (NWL per lane).
+
+__host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
+    return round16((size_t)(kmax + 1) * 8 + (size_t)kmax * nwl * 32 * 8 + (size_t)kmax * 4);
+}
+
+template <int NWL>
+__device__ __forceinline__ unsigned long long bits_expand(const JobDesc &J, int i, const int *M, uint64_t *S,
+                                                          unsigned long long &st, bool leaf, unsigned long long psum_i,
+                                                          unsigned long long &hs, unsigned long long &ab) {
+    const int lane = threadIdx.x & 31;
+    const PosInfo P = J.pos[i];
+    const int dw = J.t.dw;
+    const uint64_t *F = J.filt + (size_t)P.pv * dw;
+    const uint64_t *A = nullptr;
+    int len;
+    if (P.par >= 0) {
+        const int a = M[P.par];
+        A = J.t.adj + (size_t)a * dw;
+        len = __ldg(J.t.vld + a).y;
+    } else {
+        len = P.ucnt;
+    }
+    st += (unsigned long long)len;
+    ab += (unsigned long long)((P.par >= 0 ? 2 : 1) + P.bcnt) * (unsigned long long)dw * 8ull;
+    unsigned long long cnt = 0;
+#pragma unroll
+    for (int w = 0; w < NWL; ++w) {
+        const int q = lane + 32 * w;
+        uint64_t s = 0;
+        if (q < dw) {
+            s = F[q];
+            if (A) s &= __ldg(A + q);
+            for (int b = 0; b < P.bcnt && s; ++b) {
+                const int x = M[J.back[P.bbeg + b].pos];
+                s &= __ldg(J.t.adj + (size_t)x * dw + q);
+            }
+            for (int jj = 0; jj < i && s; ++jj) {
+                const int x = M[jj];
+                if ((x >> 6) == q) s &= ~(1ull << (x & 63));
+            }
+        }
+        cnt += __popcll(s);
+        if (leaf) {
+            uint64_t y = s;
+            while (y) {
+                const int bit = __ffsll((long long)y) - 1;
+                const int vtx = q * 64 + bit;
+                hs += fmix64(psum_i + gterm(P.pv, vtx));
+                if (J.mbuf) emit_match(J, M, i, vtx);
+                y &= y - 1;
+            }
+        } else {
+            S[w * 32 + lane] = s;
+        }
+    }
+    __syncwarp();
+    return warp_sum(cnt);
+}
+
+// Next pending survivor of a level (warp-uniform result, -1 if none); clears it.
+template <int NWL>
+__device__ __forceinline__ int bits_next(uint64_t *S) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 0; w < NWL; ++w) {
+        const uint64_t m = S[w * 32 + lane];
+        const unsigned bal = __ballot_sync(FULL, m != 0);
+        if (bal) {
+            const int L = __ffs(bal) - 1;
+            const uint64_t mw = __shfl_sync(FULL, m, L);
+            const int bit = __ffsll((long long)mw) - 1;
+            __syncwarp();
+            if (lane == L) S[w * 32 + lane] = mw & (mw - 1);
+            __syncwarp();
+            return ((L + 32 * w) << 6) + bit;
+        }
+    }
+    return -1;
+}
+
+template <int NWL>
+__global__ void __launch_bounds__(BLOCK) k_search_bits(const JobDesc *jobs, SearchCtl C, int kmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
+    unsigned long long *psum = reinterpret_cast<unsigned long long *>(base);
+    uint64_t *Sv = reinterpret_cast<uint64_t *>(psum + kmax + 1);
+    int *M = reinterpret_cast<int *>(Sv + (size_t)kmax * NWL * 32);
+
+    // the time limit counts from this warp's start on the device clock
+    const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
+    Frame fr;
+    long long iter = 0;
+    while (acquire_frame(C, M, fr, deadline)) {
+        const JobDesc &J = jobs[fr.job];
+        const int k = J.k, d0 = fr.depth;
+        unsigned long long st = 0, nd = 0, mt = 0, hs = 0, ab = 0;
+        {
+            unsigned long long s = 0;
+            for (int t = lane; t < d0; t += 32) s += gterm(J.pos[t].pv, M[t]);
+            s = warp_sum(s);
+            if (lane == 0) psum[d0] = s;
+            __syncwarp();
+        }
+        bool stopped = false;
+        if (d0 == k - 1) {
+            const unsigned long long c = bits_expand<NWL>(J, d0, M, nullptr, st, true, psum[d0], hs, ab);
+            nd += c; mt += c;
+        } else {
+            nd += bits_expand<NWL>(J, d0, M, Sv + (size_t)d0 * NWL * 32, st, false, 0, hs, ab);
+            int lvl = d0;
+            for (;;) {
+                if (((++iter) & (CHECK_EVERY - 1)) == 0) {
+                    if (C.budget > 0) {
+                        if (lane == 0) atomicAdd(J.ctr + 1, st);
+                        st = 0;
+                    }
+                    if (must_stop(C, J, st, deadline)) { stopped = true; break; }
+                    if (donation_wanted(C)) {
+                        for (int l = d0; l <= lvl; ++l) {
+                            uint64_t *Sl = Sv + (size_t)l * NWL * 32;
+                            int given = 0;
+                            while (given < C.gran) {
+                                const int v = bits_next<NWL>(Sl);
+                                if (v < 0) break;
+                                if (!push_frame(C, fr.job, l + 1, -1, -1, M, l, v)) {
+                                    // queue full: put the survivor back
+                                    if (lane == ((v >> 6) & 31)) Sl[((v >> 6) >> 5) * 32 + lane] |= 1ull << (v & 63);
+                                    __syncwarp();
+                                    given = C.gran;
+                                    break;
+                                }
+                                ++given;
+                            }
+                            if (given > 0) break;
+                        }
+                    }
+                }
+                uint64_t *Sl = Sv + (size_t)lvl * NWL * 32;
+                const int v = bits_next<NWL>(Sl);
+                if (v < 0) {
+                    if (lvl == d0) break;
+                    --lvl;
+                    continue;
+                }
+                const int pv = J.pos[lvl].pv;
+                if (lane == 0) {
+                    M[lvl] = v;
+                    psum[lvl + 1] = psum[lvl] + gterm(pv, v);
+                }
+                __syncwarp();
+                if (lvl + 1 == k - 1) {
+                    const unsigned long long c = bits_expand<NWL>(J, lvl + 1, M, nullptr, st, true, psum[lvl + 1], hs, ab);
+                    nd += c; mt += c;
+                } else {
+                    nd += bits_expand<NWL>(J, lvl + 1, M, Sv + (size_t)(lvl + 1) * NWL * 32, st, false, 0, hs, ab);
+                    ++lvl;
+                }
+            }
+        }
+        hs = warp_sum(hs);
+        if (lane == 0) {
+            atomicAdd(J.ctr + 0, mt);
+            atomicAdd(J.ctr + 1, st);
+            atomicAdd(J.ctr + 2, nd);
+            atomicAdd(J.ctr + 3, hs);
+            atomicAdd(J.abytes, ab);
+            if (!stopped) atomicSub(C.outstanding, 1);
+        }
+        __syncwarp();
+        if (stopped) break;
+    }
+}
+
+unsigned grid_for(long long warps) {
+    long long blocks = (warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    if (blocks < 1) blocks = 1;
+    return (unsigned)blocks;
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs, long long nunits,
+                               cudaStream_t st) {
+    if (nunits <= 0) return cudaSuccess;
+    k_domain_init<<<grid_for(nunits), BLOCK, 0, st>>>(jobs, unit_off, njobs, nunits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_ac(const JobDesc *jobs, const long long *unit_off, int njobs, long long nunits,
+                             int *changed, cudaStream_t st) {
+    if (nunits <= 0) return cudaSuccess;
+    k_domain_ac<<<grid_for(nunits), BLOCK, 0, st>>>(jobs, unit_off, njobs, nunits, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_fc(const JobDesc *jobs, int njobs, int *changed, cudaStream_t st) {
+    if (njobs <= 0) return cudaSuccess;
+    k_domain_fc<<<njobs, BLOCK, 0, st>>>(jobs, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs, long long nverts,
+                                long long *sizes, cudaStream_t st) {
+    if (nverts <= 0) return cudaSuccess;
+    k_domain_sizes<<<grid_for(nverts), BLOCK, 0, st>>>(jobs, vert_off, njobs, nverts, sizes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert, const int *task_out,
+                                int ntasks, int32_t *lists, cudaStream_t st) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_domain_lists<<<ntasks, BLOCK, 0, st>>>(jobs, task_job, task_vert, task_out, lists);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, int depth, int32_t *counts,
+                         const long long *offs, int32_t *fout, int pass, int count_ctr, int directed,
+                         cudaStream_t st) {
+    if (nf <= 0) return cudaSuccess;
+    long long warps = nf;
+    if (warps > 152LL * 64) warps = 152LL * 64;
+    if (directed)
+        k_split<true><<<grid_for(warps), BLOCK, 0, st>>>(jobs, fin, nf, depth, counts, offs, fout, pass, count_ctr);
+    else
+        k_split<false><<<grid_for(warps), BLOCK, 0, st>>>(jobs, fin, nf, depth, counts, offs, fout, pass, count_ctr);
+    return cudaGetLastError();
+}
+
+size_t scan_tmp_bytes(long long n) {
+    const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return (size_t)(tiles + 1) * sizeof(long long);
+}
+
+cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total, void *tmp, size_t tmp_bytes,
+                        cudaStream_t st) {
+    const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if ((size_t)(tiles + 1) * sizeof(long long) > tmp_bytes) return cudaErrorInvalidValue;
+    long long *tile_sum = static_cast<long long *>(tmp);
+    if (n <= 0) {
+        return cudaMemsetAsync(total, 0, sizeof(long long), st);
+    }
+    k_scan_tiles<<<(unsigned)tiles, BLOCK, 0, st>>>(in, out, n, tile_sum);
+    k_scan_sums<<<1, BLOCK, 0, st>>>(tile_sum, tiles, total);
+    k_scan_add<<<(unsigned)tiles, BLOCK, 0, st>>>(out, n, tile_sum);
+    return cudaGetLastError();
+}
+
+int search_warps_per_block() { return WARPS_PER_BLOCK; }
+
+namespace {
+__global__ void k_pool_init(unsigned long long *seq, int cap) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+        seq[i] = (unsigned long long)i;
+}
+}  // namespace
+
+cudaError_t launch_pool_init(unsigned long long *seq, int cap, cudaStream_t st) {
+    k_pool_init<<<(cap + BLOCK - 1) / BLOCK, BLOCK, 0, st>>>(seq, cap);
+    return cudaGetLastError();
+}
+
+size_t search_smem_bytes(int kernel, int kmax, int nwl) {
+    return WARPS_PER_BLOCK * (kernel == 2 ? bits_smem_per_warp(kmax, nwl) : csr_smem_per_warp(kmax));
+}
+
+template <typename K>
+static cudaError_t occupancy_of(K kern, size_t smem, int *occ) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, BLOCK, smem);
+}
+
+cudaError_t search_blocks_per_sm(int kernel, int kmax, int nwl, int directed, int *occ) {
+    const size_t smem = search_smem_bytes(kernel, kmax, nwl);
+    if (kernel == 2) {
+        switch (nwl) {
+            case 1: return occupancy_of(k_search_bits<1>, smem, occ);
+            case 2: return occupancy_of(k_search_bits<2>, smem, occ);
+            case 4: return occupancy_of(k_search_bits<4>, smem, occ);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (directed) return occupancy_of(k_search_csr<true>, smem, occ);
+    return occupancy_of(k_search_csr<false>, smem, occ);
+}
+
+template <typename K>
+static cudaError_t launch_persistent(K kern, const JobDesc *jobs, const SearchCtl &ctl, int kmax, size_t smem,
+                                     int blocks_per_sm, int *grid_out, cudaStream_t st) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BLOCK, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int per_sm = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
+    const int grid = sms * per_sm;
+    if (grid_out) *grid_out = grid;
+    kern<<<grid, BLOCK, smem, st>>>(jobs, ctl, kmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search(int kernel, const JobDesc *jobs, const SearchCtl &ctl, int kmax, int nwl, int directed,
+                          int blocks_per_sm, int *grid_out, cudaStream_t st) {
+    const size_t smem = search_smem_bytes(kernel, kmax, nwl);
+    if (kernel == 2) {
+        switch (nwl) {
+            case 1: return launch_persistent(k_search_bits<1>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+            case 2: return launch_persistent(k_search_bits<2>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+            case 4: return launch_persistent(k_search_bits<4>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (directed) return launch_persistent(k_search_csr<true>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+    return launch_persistent(k_search_csr<false>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+}
+
+}  // namespace sge

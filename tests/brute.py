@@ -103,6 +103,36 @@ def plant(rng: np.random.Generator, target: Graph, k: int, keep: float) -> Graph
                  np.array([int(target.vlabel[v]) for v in verts], dtype=np.int32), el, target.directed)
 
 
+def plant_connected(rng: np.random.Generator, target: Graph, k: int) -> Graph:
+    """A pattern induced on k target vertices that are connected in the
+    target's undirected view (grown from a random vertex), so the search is
+    driven by adjacency rather than by whole-vertex-set candidate lists."""
+    nb = {v: set() for v in range(target.n)}
+    for a, b in zip(target.src.tolist(), target.dst.tolist()):
+        nb[a].add(b)
+        nb[b].add(a)
+    for _ in range(100):
+        start = int(rng.integers(target.n))
+        verts, frontier = [start], sorted(nb[start])
+        while len(verts) < k and frontier:
+            x = frontier[int(rng.integers(len(frontier)))]
+            verts.append(x)
+            frontier = sorted(set(frontier).union(nb[x]).difference(verts))
+        if len(verts) == k:
+            break
+    pos = {v: i for i, v in enumerate(verts)}
+    src, dst, lab = [], [], []
+    for e in range(target.m):
+        a, b = int(target.src[e]), int(target.dst[e])
+        if a in pos and b in pos:
+            src.append(pos[a])
+            dst.append(pos[b])
+            lab.append(0 if target.elabel is None else int(target.elabel[e]))
+    el = None if target.elabel is None else np.array(lab, dtype=np.int32)
+    return Graph(len(verts), np.array(src, dtype=np.int32), np.array(dst, dtype=np.int32),
+                 np.array([int(target.vlabel[v]) for v in verts], dtype=np.int32), el, target.directed)
+
+
 def edges_graph(n: int, edges, labels=None, elabels=None, directed: bool = False) -> Graph:
     src = np.array([a for a, _ in edges], dtype=np.int32)
     dst = np.array([b for _, b in edges], dtype=np.int32)
