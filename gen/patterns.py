@@ -97,32 +97,36 @@ def dense_walk_pattern(g: Graph, k: int, stream: Stream, beta: int = 4, adj: _Ad
     adj = adj or _Adj(g)
     deg = np.diff(adj.indptr)
     starts = np.nonzero(deg > 0)[0]
+    conn = np.zeros(g.n, dtype=np.int64)      # edges from each boundary vertex into the set
+    in_set = np.zeros(g.n, dtype=bool)
     for _ in range(max_restarts):
         first = int(starts[stream.one_below(starts.shape[0])])
         chosen = [first]
-        in_set = {first}
-        conn: dict[int, int] = {}
-        for w in adj.row(first):
-            conn[int(w)] = conn.get(int(w), 0) + 1
-        while len(chosen) < k and conn:
-            cands = sorted(conn.keys())
-            weights = [conn[c] ** beta for c in cands]
-            total = sum(weights)
+        in_set[first] = True
+        keys = np.zeros(0, dtype=np.int64)    # boundary vertices, ascending
+
+        def add_boundary(x, keys):
+            row = adj.row(x)
+            row = row[~in_set[row]]
+            fresh = row[conn[row] == 0]
+            conn[row] += 1                    # rows hold no repeated neighbour
+            # both ascending and disjoint (a fresh vertex is not yet on the boundary)
+            return np.insert(keys, np.searchsorted(keys, fresh), fresh) if fresh.shape[0] else keys
+
+        keys = add_boundary(first, keys)
+        while len(chosen) < k and keys.shape[0]:
+            cum = np.cumsum(conn[keys] ** beta)
+            total = int(cum[-1])
             r = int(stream.u64(1)[0]) % total
-            acc = 0
-            pick = cands[-1]
-            for c, wgt in zip(cands, weights):
-                acc += wgt
-                if r < acc:
-                    pick = c
-                    break
+            i = int(np.searchsorted(cum, r, side="right"))
+            pick = int(keys[i])
             chosen.append(pick)
-            in_set.add(pick)
-            del conn[pick]
-            for w in adj.row(pick):
-                w = int(w)
-                if w not in in_set:
-                    conn[w] = conn.get(w, 0) + 1
+            in_set[pick] = True
+            keys = np.delete(keys, i)
+            conn[pick] = 0
+            keys = add_boundary(pick, keys)
+        conn[keys] = 0
+        in_set[np.array(chosen, dtype=np.int64)] = False
         if len(chosen) == k:
             return _induced_fast(g, adj, chosen)
     raise RuntimeError("dense walk could not reach k vertices")

@@ -69,8 +69,8 @@ enum {
 typedef struct {
     int32_t algo;              /* SGE_RI .. SGE_RIDS_SI_FC (default SGE_RI) */
     int32_t split_depth;       /* depth of the breadth-first split; 0 = auto */
-    int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 8) */
-    int32_t steal_granularity; /* most frames one donation hands out (default 8) */
+    int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 32) */
+    int32_t steal_granularity; /* most frames one donation hands out (default 2) */
     int64_t state_budget;      /* stop after about this many states (0 = none) */
     int64_t time_limit_ms;     /* stop after about this much search time (0 = none) */
     int32_t kernel;            /* SGE_KERNEL_* */

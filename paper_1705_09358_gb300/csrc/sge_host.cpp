@@ -35,6 +35,12 @@ constexpr int BITSET_MAX_N = 16384;              // adjacency bitset kept for n 
 constexpr long long FRONTIER_MAX_INTS = 1ll << 27;  // 512 MB per frontier buffer
 constexpr int POOL_CELLS = 1 << 15;
 
+// Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
+bool trace_on() {
+    static const bool on = std::getenv("SGE_TRACE") != nullptr;
+    return on;
+}
+
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
@@ -200,12 +206,12 @@ struct PatternRec {
 struct Workspace {
     DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag;
     DevBuf front[2], counts, offs, scan_tmp, total;
-    DevBuf pool, pseq, ctl;
+    DevBuf pool, pseq, ctl, slab;
     DevBuf mbuf;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void release() {
         for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
-                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &pool, &pseq, &ctl, &mbuf})
+                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &pool, &pseq, &ctl, &slab, &mbuf})
             b->release();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -601,6 +607,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         back.insert(back.end(), bq.begin(), bq.end());
     }
     if (ulist_len > INT32_MAX) return fail(ctx, SGE_ERR_OOM, "unparented candidate lists too large");
+    if (trace_on())
+        std::fprintf(stderr, "[sge] jobs %d kernel %d kmax %d nwl %d filt_words %lld domains %.3f ms\n", nj, kernel,
+                     kmax, nwl, filt_words, now_ms() - t_start);
     CK(upload(W.pos, pos, st), "upload positions");
     CK(upload(W.back, back, st), "upload back edges");
     CK(W.ulist.ensure((size_t)std::max<long long>(ulist_len, 1) * 4), "alloc lists");
@@ -641,7 +650,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     CK(search_blocks_per_sm(kernel == SGE_KERNEL_BITSET ? 2 : 1, kmax, nwl, directed ? 1 : 0, &occ), "occupancy");
     if (o.blocks_per_sm > 0 && o.blocks_per_sm < occ) occ = o.blocks_per_sm;
     const long long resident_warps = (long long)ctx->sms * occ * search_warps_per_block();
-    const long long fpw = o.frames_per_warp > 0 ? o.frames_per_warp : 8;
+    const long long fpw = o.frames_per_warp > 0 ? o.frames_per_warp : 32;
     const long long target_frames = fpw * resident_warps * shard_count;
     std::vector<int32_t> f0;
     for (int q = 0; q < nj; ++q)
@@ -678,6 +687,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         cur ^= 1;
         F = total;
         ++depth;
+        if (trace_on()) std::fprintf(stderr, "[sge] split depth %d frames %lld at %.3f ms\n", depth, F, now_ms() - t_start);
     }
 
     // ------------------------------------------------- persistent search
@@ -718,15 +728,22 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         C.deadline_ns = o.time_limit_ms > 0 ? (unsigned long long)o.time_limit_ms * 1000000ull : 0ull;
         C.budget = o.state_budget;
         C.donate = o.no_donation ? 0 : 1;
-        C.gran = o.steal_granularity > 0 ? o.steal_granularity : 8;
+        C.gran = o.steal_granularity > 0 ? o.steal_granularity : 2;
         if (!W.ev0) {
             CK(cudaEventCreate(&W.ev0), "event");
             CK(cudaEventCreate(&W.ev1), "event");
         }
         int grid = 0;
+        const int kfam = kernel == SGE_KERNEL_BITSET ? 2 : 1;
+        const long long max_grid = (long long)ctx->sms * occ;
+        const size_t slab_bytes = search_slab_bytes(kfam, kmax, nwl, max_grid);
+        if (slab_bytes > 0) {
+            CK(W.slab.ensure(slab_bytes), "alloc search slab");
+            C.slab = W.slab.as<uint64_t>();
+        }
         CK(cudaEventRecord(W.ev0, st), "event record");
-        CK(launch_search(kernel == SGE_KERNEL_BITSET ? 2 : 1, W.jobs.as<JobDesc>(), C, kmax, nwl, directed ? 1 : 0,
-                         o.blocks_per_sm, &grid, st), "search launch");
+        CK(launch_search(kfam, W.jobs.as<JobDesc>(), C, kmax, nwl, directed ? 1 : 0, o.blocks_per_sm, max_grid, &grid,
+                         st), "search launch");
         ++launches;
         CK(cudaEventRecord(W.ev1, st), "event record");
         unsigned long long dn = 0;
@@ -735,6 +752,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         CK(cudaStreamSynchronize(st), "search sync");
         CK(cudaEventElapsedTime(&kernel_ms, W.ev0, W.ev1), "event time");
         donations = (long long)dn;
+        if (trace_on())
+            std::fprintf(stderr, "[sge] search grid %d frames %lld kernel %.3f ms status %d donations %llu\n", grid,
+                         nfront, kernel_ms, status, dn);
     }
     std::vector<unsigned long long> ctr((size_t)nj * 6);
     CK(cudaMemcpyAsync(ctr.data(), W.ctr.p, (size_t)nj * 6 * 8, cudaMemcpyDeviceToHost, st), "read counters");

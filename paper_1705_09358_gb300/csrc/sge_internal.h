@@ -121,6 +121,7 @@ struct SearchCtl {
     long long budget;           // states budget per job, 0 = none
     int32_t donate;             // work donation on/off
     int32_t gran;               // most frames per donation
+    uint64_t *slab;             // bitset kernel: per-warp level bitsets (search_slab_bytes)
 };
 
 // ------------------------------------------------------------ launchers
@@ -146,11 +147,14 @@ cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long lon
 size_t scan_tmp_bytes(long long n);
 
 // Persistent search.  kernel: 1 = CSR, 2 = bitset.  Returns the grid size used.
+// The grid is capped at `max_grid` blocks (the blocks the slab was sized for; 0 = no cap).
 cudaError_t launch_search(int kernel, const JobDesc *jobs, const SearchCtl &ctl, int kmax, int nwl,
-                          int directed, int blocks_per_sm, int *grid_out, cudaStream_t st);
+                          int directed, int blocks_per_sm, long long max_grid, int *grid_out, cudaStream_t st);
 int search_warps_per_block();
 cudaError_t search_blocks_per_sm(int kernel, int kmax, int nwl, int directed, int *occ);
 cudaError_t launch_pool_init(unsigned long long *seq, int cap, cudaStream_t st);
 size_t search_smem_bytes(int kernel, int kmax, int nwl);
+// Global scratch the search kernel needs for a grid of `grid` blocks.
+size_t search_slab_bytes(int kernel, int kmax, int nwl, long long grid);
 
 }  // namespace sge

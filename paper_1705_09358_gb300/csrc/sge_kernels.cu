@@ -32,6 +32,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int BLOCK = WARPS_PER_BLOCK * 32;
 constexpr int CHECK_EVERY = 64;          // iterations between donation / abort checks
+constexpr int DONATE_BACKOFF = 1024;     // iterations without donating after a donation
+constexpr int DONATE_MIN_LEVELS = 2;     // a donated node keeps at least this many levels below it
 constexpr long long IDLE_SPIN_LIMIT = 1ll << 31;
 constexpr int QUEUE_ATTEMPTS = 64;
 
@@ -589,6 +591,7 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
     const int lane = threadIdx.x & 31;
     bool idle = false;
     long long spins = 0;
+    unsigned backoff = 64;
     int kind = 0;        // 1 frontier, 2 queue, 0 stop
     long long idx = -1;
     for (;;) {
@@ -618,7 +621,9 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
         }
         kind = __shfl_sync(FULL, kind, 0);
         if (kind >= 0) break;
-        __nanosleep(200);
+        // exponential backoff keeps idle warps from crowding the queue's cache lines
+        __nanosleep(backoff);
+        if (backoff < 8192) backoff <<= 1;
     }
     if (lane == 0 && idle) atomicSub(C.idle, 1);
     if (kind == 0) return false;
@@ -699,7 +704,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
     // the time limit counts from this warp's start on the device clock
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
-    long long iter = 0;
+    long long iter = 0, quiet_until = 0;
     while (acquire_frame(C, M, fr, deadline)) {
         const JobDesc &J = jobs[fr.job];
         const int k = J.k, d0 = fr.depth;
@@ -728,10 +733,11 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                     st = 0;
                 }
                 if (must_stop(C, J, st, deadline)) { stopped = true; break; }
-                if (donation_wanted(C)) {
+                if (iter >= quiet_until && donation_wanted(C)) {
                     // donate the shallowest unexplored work: half of an unscanned
                     // range, else up to `gran` pending survivors as new search nodes
-                    for (int l = d0; l <= lvl; ++l) {
+                    quiet_until = iter + DONATE_BACKOFF;
+                    for (int l = d0; l <= lvl && l + 1 + DONATE_MIN_LEVELS <= k; ++l) {
                         LvCsr &L = lv[l];
                         const int rem = L.end - L.cur;
                         if (rem >= 64) {
@@ -827,72 +833,165 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 // ================================================== search: bitset kernel
 //
 // Candidate set of position i as one AND over bitset rows (dense targets):
-//   S_i = D(mu_i) & A[M(P(mu_i))] & AND_j A[M(mu_j)] & ~{M_0..M_{i-1}}
-// where D is the domain (RI-DS) or the label/degree filter (RI) and A the
-// adjacency bitset.  Lane l owns words l, l + 32, ... (NWL per lane).
+//   S_i = D(mu_i) & A[M(P(mu_i))] & AND_j A[M(mu_j)] & ~used
+// where D is the domain (RI-DS) or the label/degree filter (RI), A the
+// adjacency bitset and `used` the images M_0..M_{i-1} (rule 1).  Lane l owns
+// words l, l + 32, ... (NWL per lane).
+//
+// Per warp, shared memory holds the used bitset, M, the hash prefixes, a
+// compact copy of the job's position table, and for every level a list of
+// up to LIST_CAP pending survivors; a level with more survivors keeps its
+// bitset in the warp's slab of global scratch (`SearchCtl::slab`) instead.
+
+constexpr int LIST_CAP = 16;
+constexpr uint8_t LIST_SPILLED = 0xff;
+
+struct PosB {
+    int16_t pv, par, bb, bc;  // pattern vertex, parent position, back-edge range
+    int32_t ucnt;             // raw candidates of an unparented position
+};
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
-    return round16((size_t)(kmax + 1) * 8 + (size_t)kmax * nwl * 32 * 8 + (size_t)kmax * 4);
+    return round16((size_t)(kmax + 1) * 8 +                 // psum
+                   (size_t)nwl * 32 * 8 +                   // used bitset
+                   (size_t)kmax * 4 +                       // M
+                   (size_t)kmax * sizeof(PosB) +            // position table
+                   (size_t)kmax * LIST_CAP * 2 +            // survivor lists
+                   (size_t)kmax +                           // list lengths
+                   (size_t)kmax * (kmax - 1) / 2 + 16);     // back-edge positions
+}
+
+__host__ __device__ __forceinline__ size_t bits_slab_words_per_warp(int kmax, int nwl) {
+    return (size_t)kmax * nwl * 32;
+}
+
+struct BitsJob {
+    const uint64_t *filt, *adj;
+    const int2 *vld;
+    int dw, k;
+};
+
+struct BitsWarp {
+    unsigned long long *psum;
+    uint64_t *used;
+    int *M;
+    PosB *tab;
+    uint16_t *lst;     // [kmax][LIST_CAP]
+    uint8_t *lcnt;     // [kmax]
+    uint8_t *tback;
+    uint64_t *slab;    // global: [kmax][NWL * 32]
+};
+
+template <int NWL>
+__device__ __forceinline__ void used_flip(uint64_t *used, int v) {
+    const int q = v >> 6;
+    if ((threadIdx.x & 31) == (q & 31)) used[(q >> 5) * 32 + (q & 31)] ^= 1ull << (v & 63);
 }
 
 template <int NWL>
-__device__ __forceinline__ unsigned long long bits_expand(const JobDesc &J, int i, const int *M, uint64_t *S,
-                                                          unsigned long long &st, bool leaf, unsigned long long psum_i,
-                                                          unsigned long long &hs, unsigned long long &ab) {
+__device__ __forceinline__ unsigned long long bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W, int i,
+                                                          bool leaf, unsigned long long &st, unsigned long long &hs,
+                                                          unsigned long long &ab) {
     const int lane = threadIdx.x & 31;
-    const PosInfo P = J.pos[i];
-    const int dw = J.t.dw;
-    const uint64_t *F = J.filt + (size_t)P.pv * dw;
-    const uint64_t *A = nullptr;
-    int len;
-    if (P.par >= 0) {
-        const int a = M[P.par];
-        A = J.t.adj + (size_t)a * dw;
-        len = __ldg(J.t.vld + a).y;
-    } else {
-        len = P.ucnt;
-    }
-    st += (unsigned long long)len;
-    ab += (unsigned long long)((P.par >= 0 ? 2 : 1) + P.bcnt) * (unsigned long long)dw * 8ull;
-    unsigned long long cnt = 0;
+    const PosB p = W.tab[i];
+    const int dw = B.dw;
+    const uint64_t *F = B.filt + (size_t)p.pv * dw;
+    const int *M = W.M;
+    uint64_t s[NWL];
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
         const int q = lane + 32 * w;
-        uint64_t s = 0;
-        if (q < dw) {
-            s = F[q];
-            if (A) s &= __ldg(A + q);
-            for (int b = 0; b < P.bcnt && s; ++b) {
-                const int x = M[J.back[P.bbeg + b].pos];
-                s &= __ldg(J.t.adj + (size_t)x * dw + q);
-            }
-            for (int jj = 0; jj < i && s; ++jj) {
-                const int x = M[jj];
-                if ((x >> 6) == q) s &= ~(1ull << (x & 63));
-            }
+        s[w] = q < dw ? F[q] : 0ull;
+    }
+    int len = p.ucnt;
+    if (p.par >= 0) {
+        const int a = M[p.par];
+        const uint64_t *A = B.adj + (size_t)a * dw;
+#pragma unroll
+        for (int w = 0; w < NWL; ++w) {
+            const int q = lane + 32 * w;
+            if (q < dw) s[w] &= __ldg(A + q);
         }
-        cnt += __popcll(s);
-        if (leaf) {
-            uint64_t y = s;
+        len = __ldg(B.vld + a).y;
+    }
+#pragma unroll 4
+    for (int b = 0; b < p.bc; ++b) {
+        const uint64_t *X = B.adj + (size_t)M[W.tback[p.bb + b]] * dw;
+#pragma unroll
+        for (int w = 0; w < NWL; ++w) {
+            const int q = lane + 32 * w;
+            if (q < dw) s[w] &= __ldg(X + q);
+        }
+    }
+    st += (unsigned long long)len;
+    ab += (unsigned long long)((p.par >= 0 ? 2 : 1) + p.bc) * (unsigned long long)dw * 8ull;
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < NWL; ++w) {
+        s[w] &= ~W.used[w * 32 + lane];
+        cnt += __popcll(s[w]);
+    }
+    if (leaf) {
+        const unsigned long long psum_i = W.psum[i];
+#pragma unroll
+        for (int w = 0; w < NWL; ++w) {
+            const int q = lane + 32 * w;
+            uint64_t y = s[w];
             while (y) {
                 const int bit = __ffsll((long long)y) - 1;
                 const int vtx = q * 64 + bit;
-                hs += fmix64(psum_i + gterm(P.pv, vtx));
+                hs += fmix64(psum_i + gterm(p.pv, vtx));
                 if (J.mbuf) emit_match(J, M, i, vtx);
                 y &= y - 1;
             }
-        } else {
-            S[w * 32 + lane] = s;
         }
+        return warp_sum((unsigned long long)cnt);
+    }
+    // pending survivors: a short list in shared memory, else the bitset in the slab
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (total <= LIST_CAP) {
+        uint16_t *L = W.lst + i * LIST_CAP;
+        int o = incl - cnt;
+#pragma unroll
+        for (int w = 0; w < NWL; ++w) {
+            const int q = lane + 32 * w;
+            uint64_t y = s[w];
+            while (y) {
+                L[o++] = (uint16_t)(q * 64 + __ffsll((long long)y) - 1);
+                y &= y - 1;
+            }
+        }
+        if (lane == 0) W.lcnt[i] = (uint8_t)total;
+    } else {
+        uint64_t *Sl = W.slab + (size_t)i * NWL * 32;
+#pragma unroll
+        for (int w = 0; w < NWL; ++w) Sl[w * 32 + lane] = s[w];
+        if (lane == 0) W.lcnt[i] = LIST_SPILLED;
     }
     __syncwarp();
-    return warp_sum(cnt);
+    return (unsigned long long)total;
 }
 
-// Next pending survivor of a level (warp-uniform result, -1 if none); clears it.
+// Next pending survivor of level l (warp-uniform, -1 if none); removes it.
 template <int NWL>
-__device__ __forceinline__ int bits_next(uint64_t *S) {
+__device__ __forceinline__ int bits_next(const BitsWarp &W, int l) {
     const int lane = threadIdx.x & 31;
+    const int c = W.lcnt[l];
+    if (c != LIST_SPILLED) {
+        if (c == 0) return -1;
+        const int v = W.lst[l * LIST_CAP + c - 1];
+        __syncwarp();
+        if (lane == 0) W.lcnt[l] = (uint8_t)(c - 1);
+        __syncwarp();
+        return v;
+    }
+    uint64_t *S = W.slab + (size_t)l * NWL * 32;
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
         const uint64_t m = S[w * 32 + lane];
@@ -910,36 +1009,79 @@ __device__ __forceinline__ int bits_next(uint64_t *S) {
     return -1;
 }
 
+// Put a survivor back at level l (the donation queue was full).
 template <int NWL>
-__global__ void __launch_bounds__(BLOCK) k_search_bits(const JobDesc *jobs, SearchCtl C, int kmax) {
+__device__ __forceinline__ void bits_unnext(const BitsWarp &W, int l, int v) {
+    const int lane = threadIdx.x & 31;
+    const int c = W.lcnt[l];
+    __syncwarp();
+    if (c != LIST_SPILLED) {
+        if (lane == 0) { W.lst[l * LIST_CAP + c] = (uint16_t)v; W.lcnt[l] = (uint8_t)(c + 1); }
+    } else {
+        const int q = v >> 6;
+        if (lane == (q & 31)) W.slab[(size_t)l * NWL * 32 + (q >> 5) * 32 + lane] |= 1ull << (v & 63);
+    }
+    __syncwarp();
+}
+
+template <int NWL>
+__global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, SearchCtl C, int kmax) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
-    unsigned long long *psum = reinterpret_cast<unsigned long long *>(base);
-    uint64_t *Sv = reinterpret_cast<uint64_t *>(psum + kmax + 1);
-    int *M = reinterpret_cast<int *>(Sv + (size_t)kmax * NWL * 32);
+    BitsWarp W;
+    W.psum = reinterpret_cast<unsigned long long *>(base);
+    W.used = reinterpret_cast<uint64_t *>(W.psum + kmax + 1);
+    W.M = reinterpret_cast<int *>(W.used + NWL * 32);
+    W.tab = reinterpret_cast<PosB *>(W.M + kmax);
+    W.lst = reinterpret_cast<uint16_t *>(W.tab + kmax);
+    W.lcnt = reinterpret_cast<uint8_t *>(W.lst + (size_t)kmax * LIST_CAP);
+    W.tback = W.lcnt + kmax;
+    W.slab = C.slab + ((size_t)blockIdx.x * WARPS_PER_BLOCK + wib) * bits_slab_words_per_warp(kmax, NWL);
+    int *M = W.M;
 
-    // the time limit counts from this warp's start on the device clock
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
-    long long iter = 0;
+    long long iter = 0, quiet_until = 0;
+    int cur_job = -1;
+    BitsJob B;
     while (acquire_frame(C, M, fr, deadline)) {
         const JobDesc &J = jobs[fr.job];
-        const int k = J.k, d0 = fr.depth;
+        if (fr.job != cur_job) {
+            // cache the job's pointers in registers and its position table in shared memory
+            cur_job = fr.job;
+            B.filt = J.filt; B.adj = J.t.adj; B.vld = J.t.vld; B.dw = J.t.dw; B.k = J.k;
+            for (int t = lane; t < B.k; t += 32) {
+                const PosInfo P = J.pos[t];
+                PosB q;
+                q.pv = (int16_t)P.pv; q.par = (int16_t)P.par; q.bb = (int16_t)P.bbeg; q.bc = (int16_t)P.bcnt;
+                q.ucnt = P.ucnt;
+                W.tab[t] = q;
+            }
+            __syncwarp();
+            const int nb = W.tab[B.k - 1].bb + W.tab[B.k - 1].bc;
+            for (int b = lane; b < nb; b += 32) W.tback[b] = (uint8_t)J.back[b].pos;
+            __syncwarp();
+        }
+        const int k = B.k, d0 = fr.depth;
         unsigned long long st = 0, nd = 0, mt = 0, hs = 0, ab = 0;
         {
             unsigned long long s = 0;
-            for (int t = lane; t < d0; t += 32) s += gterm(J.pos[t].pv, M[t]);
+            for (int t = lane; t < d0; t += 32) s += gterm(W.tab[t].pv, M[t]);
             s = warp_sum(s);
-            if (lane == 0) psum[d0] = s;
+#pragma unroll
+            for (int w = 0; w < NWL; ++w) W.used[w * 32 + lane] = 0ull;
+            __syncwarp();
+            for (int t = 0; t < d0; ++t) used_flip<NWL>(W.used, M[t]);
+            if (lane == 0) { W.psum[d0] = s; M[d0] = -1; }
             __syncwarp();
         }
         bool stopped = false;
         if (d0 == k - 1) {
-            const unsigned long long c = bits_expand<NWL>(J, d0, M, nullptr, st, true, psum[d0], hs, ab);
+            const unsigned long long c = bits_expand<NWL>(B, J, W, d0, true, st, hs, ab);
             nd += c; mt += c;
         } else {
-            nd += bits_expand<NWL>(J, d0, M, Sv + (size_t)d0 * NWL * 32, st, false, 0, hs, ab);
+            nd += bits_expand<NWL>(B, J, W, d0, false, st, hs, ab);
             int lvl = d0;
             for (;;) {
                 if (((++iter) & (CHECK_EVERY - 1)) == 0) {
@@ -948,17 +1090,16 @@ __global__ void __launch_bounds__(BLOCK) k_search_bits(const JobDesc *jobs, Sear
                         st = 0;
                     }
                     if (must_stop(C, J, st, deadline)) { stopped = true; break; }
-                    if (donation_wanted(C)) {
-                        for (int l = d0; l <= lvl; ++l) {
-                            uint64_t *Sl = Sv + (size_t)l * NWL * 32;
+                    if (iter >= quiet_until && donation_wanted(C)) {
+                        // donate up to `gran` pending survivors of the shallowest level that has some
+                        quiet_until = iter + DONATE_BACKOFF;
+                        for (int l = d0; l <= lvl && l + 1 + DONATE_MIN_LEVELS <= k; ++l) {
                             int given = 0;
                             while (given < C.gran) {
-                                const int v = bits_next<NWL>(Sl);
+                                const int v = bits_next<NWL>(W, l);
                                 if (v < 0) break;
                                 if (!push_frame(C, fr.job, l + 1, -1, -1, M, l, v)) {
-                                    // queue full: put the survivor back
-                                    if (lane == ((v >> 6) & 31)) Sl[((v >> 6) >> 5) * 32 + lane] |= 1ull << (v & 63);
-                                    __syncwarp();
+                                    bits_unnext<NWL>(W, l, v);
                                     given = C.gran;
                                     break;
                                 }
@@ -968,25 +1109,30 @@ __global__ void __launch_bounds__(BLOCK) k_search_bits(const JobDesc *jobs, Sear
                         }
                     }
                 }
-                uint64_t *Sl = Sv + (size_t)lvl * NWL * 32;
-                const int v = bits_next<NWL>(Sl);
+                const int prev = M[lvl];
+                if (prev >= 0) used_flip<NWL>(W.used, prev);      // leave the previous choice at this level
+                const int v = bits_next<NWL>(W, lvl);
                 if (v < 0) {
+                    if (lane == 0) M[lvl] = -1;
+                    __syncwarp();
                     if (lvl == d0) break;
                     --lvl;
                     continue;
                 }
-                const int pv = J.pos[lvl].pv;
+                used_flip<NWL>(W.used, v);
                 if (lane == 0) {
                     M[lvl] = v;
-                    psum[lvl + 1] = psum[lvl] + gterm(pv, v);
+                    W.psum[lvl + 1] = W.psum[lvl] + gterm(W.tab[lvl].pv, v);
                 }
                 __syncwarp();
                 if (lvl + 1 == k - 1) {
-                    const unsigned long long c = bits_expand<NWL>(J, lvl + 1, M, nullptr, st, true, psum[lvl + 1], hs, ab);
+                    const unsigned long long c = bits_expand<NWL>(B, J, W, lvl + 1, true, st, hs, ab);
                     nd += c; mt += c;
                 } else {
-                    nd += bits_expand<NWL>(J, lvl + 1, M, Sv + (size_t)(lvl + 1) * NWL * 32, st, false, 0, hs, ab);
+                    nd += bits_expand<NWL>(B, J, W, lvl + 1, false, st, hs, ab);
                     ++lvl;
+                    if (lane == 0) M[lvl] = -1;
+                    __syncwarp();
                 }
             }
         }
@@ -1098,6 +1244,11 @@ size_t search_smem_bytes(int kernel, int kmax, int nwl) {
     return WARPS_PER_BLOCK * (kernel == 2 ? bits_smem_per_warp(kmax, nwl) : csr_smem_per_warp(kmax));
 }
 
+size_t search_slab_bytes(int kernel, int kmax, int nwl, long long grid) {
+    if (kernel != 2) return 0;
+    return (size_t)grid * WARPS_PER_BLOCK * bits_slab_words_per_warp(kmax, nwl) * sizeof(uint64_t);
+}
+
 template <typename K>
 static cudaError_t occupancy_of(K kern, size_t smem, int *occ) {
     if (smem > 48 * 1024) {
@@ -1123,7 +1274,7 @@ cudaError_t search_blocks_per_sm(int kernel, int kmax, int nwl, int directed, in
 
 template <typename K>
 static cudaError_t launch_persistent(K kern, const JobDesc *jobs, const SearchCtl &ctl, int kmax, size_t smem,
-                                     int blocks_per_sm, int *grid_out, cudaStream_t st) {
+                                     int blocks_per_sm, long long max_grid, int *grid_out, cudaStream_t st) {
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1137,25 +1288,27 @@ static cudaError_t launch_persistent(K kern, const JobDesc *jobs, const SearchCt
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int per_sm = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
-    const int grid = sms * per_sm;
+    long long g = (long long)sms * per_sm;
+    if (max_grid > 0 && g > max_grid) g = max_grid;   // never more blocks than the scratch slab covers
+    const int grid = (int)g;
     if (grid_out) *grid_out = grid;
     kern<<<grid, BLOCK, smem, st>>>(jobs, ctl, kmax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_search(int kernel, const JobDesc *jobs, const SearchCtl &ctl, int kmax, int nwl, int directed,
-                          int blocks_per_sm, int *grid_out, cudaStream_t st) {
+                          int blocks_per_sm, long long max_grid, int *grid_out, cudaStream_t st) {
     const size_t smem = search_smem_bytes(kernel, kmax, nwl);
     if (kernel == 2) {
         switch (nwl) {
-            case 1: return launch_persistent(k_search_bits<1>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
-            case 2: return launch_persistent(k_search_bits<2>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
-            case 4: return launch_persistent(k_search_bits<4>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+            case 1: return launch_persistent(k_search_bits<1>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
+            case 2: return launch_persistent(k_search_bits<2>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
+            case 4: return launch_persistent(k_search_bits<4>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
             default: return cudaErrorInvalidValue;
         }
     }
-    if (directed) return launch_persistent(k_search_csr<true>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
-    return launch_persistent(k_search_csr<false>, jobs, ctl, kmax, smem, blocks_per_sm, grid_out, st);
+    if (directed) return launch_persistent(k_search_csr<true>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
+    return launch_persistent(k_search_csr<false>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
 }
 
 }  // namespace sge

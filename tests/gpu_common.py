@@ -23,6 +23,27 @@ def engine():
     return _ctx
 
 
+_cache = {}
+
+
+def workload(name: str, **kw):
+    """Generated workloads, built once per test session."""
+    from gen import configs
+    key = (name, tuple(sorted(kw.items())))
+    if key not in _cache:
+        if name == "cl100k_target":
+            _cache[key] = configs.cl100k_target()
+        elif name == "cl100k":
+            _cache[key] = configs.cl100k(count=5000, target=workload("cl100k_target"))
+        elif name == "mol_targets":
+            _cache[key] = configs.mol_targets(200)
+        elif name == "mol_patterns":
+            _cache[key] = configs.mol_patterns(workload("mol_targets"), 1000)
+        else:
+            _cache[key] = configs.BUILDERS[name](**kw)
+    return _cache[key]
+
+
 def counters(d) -> tuple:
     return tuple(int(d[k]) for k in KEYS)
 

@@ -154,7 +154,12 @@ def test_cl10k_all_patterns():
 
 
 # --------------------------------------------- schedule independence
-def test_schedule_invariance():
+SCHEDULES = [dict(split_depth=1), dict(split_depth=3), dict(frames_per_warp=1), dict(frames_per_warp=64),
+             dict(steal_granularity=1), dict(steal_granularity=64), dict(no_donation=1), dict(blocks_per_sm=1),
+             dict(blocks_per_sm=2, frames_per_warp=2)]
+
+
+def test_schedule_invariance_csr():
     """Counters are fixed by the search tree: every split depth, frame count,
     donation granularity and grid size must give the same four numbers."""
     w = configs.cl10k()
@@ -162,10 +167,19 @@ def test_schedule_invariance():
     tid = E.load_target(w.targets[0])
     pid = E.load_pattern(w.patterns[4])
     base = counters(E.count(tid, pid, algo=3))
-    for opts in [dict(split_depth=1), dict(split_depth=3), dict(frames_per_warp=1), dict(frames_per_warp=64),
-                 dict(steal_granularity=1), dict(no_donation=1), dict(blocks_per_sm=1), dict(kernel=1),
-                 dict(kernel=2)]:
+    for opts in SCHEDULES:
         assert counters(E.count(tid, pid, algo=3, **opts)) == base, opts
+
+
+def test_schedule_invariance_bitset():
+    w = configs.er2000()
+    g = golden("er2000")["patterns"][1]
+    E = engine()
+    tid = E.load_target(w.targets[0])
+    pid = E.load_pattern(w.patterns[1])
+    want = golden_counters(g["algos"]["3"])
+    for opts in SCHEDULES + [dict(kernel=1), dict(kernel=2)]:
+        assert counters(E.count(tid, pid, algo=3, **opts)) == want, opts
 
 
 def test_shards_sum_to_whole():

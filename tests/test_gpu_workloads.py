@@ -1,0 +1,131 @@
+"""Full-size parity on the five synthetic workloads, in the launch
+configurations the bench uses, against the oracle's stored results
+(tests/golden/expected_*.json, written by tests/golden/make_expected.py)."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from brute import complete
+from gen import configs
+from gpu_common import engine, counters, golden, golden_counters, table_digest, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def test_er2000_single_and_batched():
+    w = configs.er2000()
+    g = golden("er2000")
+    assert w.targets[0].sha256() == g["target_sha256"]
+    E = engine()
+    tid = E.load_target(w.targets[0])
+    pids = [E.load_pattern(p) for p in w.patterns]
+    for ent, p in zip(g["patterns"], w.patterns):
+        assert p.sha256() == ent["pattern_sha256"]
+    # the bench's configuration: all five pairs in one batched call, RI-DS-SI-FC
+    rc, rows = E.count_batch([tid] * 5, pids, algo=3)
+    for ent, row in zip(g["patterns"], rows):
+        assert counters(row) == golden_counters(ent["algos"]["3"]), ent["slot"]
+    # every variant, both kernel families, one pattern at a time
+    for ent, pid in zip(g["patterns"], pids):
+        for algo in range(4):
+            want = ent["algos"][str(algo)]
+            if want is None:
+                continue
+            for kern in (1, 2):
+                got = E.count(tid, pid, algo=algo, kernel=kern)
+                assert counters(got) == golden_counters(want), (ent["slot"], algo, kern)
+
+
+@pytest.mark.parametrize("algo", [0, 3])
+def test_mol200_all_pairs_batched(algo):
+    ts = workload("mol_targets")
+    ps = workload("mol_patterns")
+    g = golden("mol200")
+    E = engine()
+    tids = [E.load_target(t) for t in ts]
+    pids = [E.load_pattern(p) for p in ps]
+    T = np.repeat(np.array(tids, np.int32), len(pids))
+    P = np.tile(np.array(pids, np.int32), len(tids))
+    rc, rows = E.count_batch(T, P, algo=algo)
+    table = np.stack([rows["matches"], rows["states"], rows["nodes"], rows["hash"]], axis=1).astype(np.uint64)
+    want = g["algos"][str(algo)]
+    sample = np.array(want["sample_every_997"], dtype=np.uint64)
+    assert np.array_equal(table[::997], sample)
+    assert int(table[:, 1].sum()) == want["totals"]["states"]
+    assert table_digest(table) == want["per_pair_sha256"]
+
+
+def test_cl100k_queries_batched_and_alone():
+    g = golden("cl100k")
+    t = workload("cl100k_target")
+    assert t.sha256() == g["target_sha256"]
+    w = workload("cl100k")
+    E = engine()
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in w.patterns[:200]]
+    rc, rows = E.count_batch([tid] * len(pids), pids, algo=0)
+    want = np.array(g["first_200"], dtype=np.uint64)
+    got = np.stack([rows["matches"], rows["states"], rows["nodes"], rows["hash"]], axis=1).astype(np.uint64)
+    assert np.array_equal(got, want)
+    for i in range(0, 200, 20):
+        assert counters(E.count(tid, pids[i], algo=0)) == tuple(int(x) for x in want[i]), i
+
+
+def test_cl100k_all_5000_digest():
+    g = golden("cl100k")
+    t = workload("cl100k_target")
+    w = workload("cl100k")
+    E = engine()
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in w.patterns]
+    rc, rows = E.count_batch([tid] * len(pids), pids, algo=0)
+    table = np.stack([rows["matches"], rows["states"], rows["nodes"], rows["hash"]], axis=1).astype(np.uint64)
+    assert int(table[:, 1].sum()) == g["totals"]["states"]
+    assert table_digest(table) == g["per_query_sha256"]
+
+
+def test_serving_results_same_alone_and_in_mix():
+    """Queries submitted while others run are admitted, batched and overlapped;
+    every result equals the query's result run alone (and the oracle's)."""
+    g = golden("cl100k")
+    t = workload("cl100k_target")
+    w = workload("cl100k")
+    E = engine()
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in w.patterns[:200]]
+    tickets = []
+    for i, pid in enumerate(pids):
+        tickets.append(E.serve_submit(tid, pid, algo=0))
+        if i % 16 == 15:
+            time.sleep(0.001)
+    E.serve_drain()
+    want = np.array(g["first_200"], dtype=np.uint64)
+    for i, tk in enumerate(tickets):
+        r = E.serve_poll(tk)
+        assert r is not None and r["status"] == 0
+        assert counters(r) == tuple(int(x) for x in want[i]), i
+    for i in range(0, 200, 25):
+        assert counters(E.count(tid, pids[i], algo=0)) == tuple(int(x) for x in want[i])
+
+
+def test_cancel_from_another_thread():
+    import paper_1705_09358_gb300 as sge
+    E = engine()
+    tid, pid = E.load_target(complete(48)), E.load_pattern(complete(9))
+    out = {}
+
+    def run():
+        out["r"] = E.count(tid, pid, check=False)
+
+    th = threading.Thread(target=run)
+    th.start()
+    time.sleep(1.0)
+    E.cancel()
+    th.join(timeout=120)
+    assert not th.is_alive()
+    assert out["r"]["rc"] == sge.SGE_ERR_CANCELLED
+    assert E.count(tid, E.load_pattern(complete(2)))["matches"] == 48 * 47
