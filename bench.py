@@ -263,9 +263,9 @@ def run_ours(args, world, rank, local):
             "gpu_launches": launches, "roofline": roofline, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_extras:
         line["batched_vs_per_query"] = batched_vs_per_query(E, args)
-        smp = oracle_sample(w, 60_000_000)
+        smp = oracle_sample(w, 200_000_000)
         line["cpu_baseline"] = {"value": smp["states"] / smp["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "the oracle (one thread) on all 5 patterns, each stopped after 6e7 states; "
+                                "sample": "the oracle (one thread) on all 5 patterns, each stopped after 2e8 states; "
                                           f"{smp['states']} states in {smp['seconds']:.1f} s"}
     with Clocks(local) as _:
         pass
