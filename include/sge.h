@@ -180,6 +180,45 @@ sge_status sge_serve_poll(sge_ctx *ctx, int64_t ticket, int32_t *done, sge_resul
 /* Block until every submitted query finished. */
 sge_status sge_serve_drain(sge_ctx *ctx);
 
+/* Count without allocating: a variant of sge_count for callers that cannot
+ * allocate device memory at the time they search (code under a memory
+ * manager that owns every device allocation, an allocator at its limit, or
+ * a runtime that forbids cudaMalloc/cudaFree on its threads).  The paper has
+ * no counterpart; this is an interface for such callers.
+ *
+ * The caller passes the inputs and the output: an undirected target already
+ * in device memory as CSR (d_rowptr[n+1], d_col[d_rowptr[n]] with every
+ * edge stored in both rows and each row sorted ascending, d_vlabel[n],
+ * d_elabel parallel to d_col or NULL for all 0), the pattern as host arrays
+ * (k <= 128 vertices, m edges as for sge_load_pattern), and out[4] in host
+ * memory, which receives matches, states, nodes and hash as sge_count
+ * defines them for SGE_RI.  The search is RI on the CSR kernel, started
+ * from the root with work donation; it runs on `cuda_stream` (NULL = the
+ * default stream) and the call returns once the counters are in `out`.
+ * time_limit_ms <= 0 means none.
+ *
+ * Nothing is allocated: every device-side buffer the search needs (its job
+ * record, counters, position tables, root frame, a 2048-frame work queue
+ * and the per-vertex label/degree records, 8 bytes per target vertex) is
+ * carved from one fixed 16 MiB array in the library's device memory, which
+ * every GPU that loads the library holds until the process exits.  A
+ * target too large for that array (about 1.9 million vertices; fewer if
+ * the pattern has edge labels and the target has none) is rejected with
+ * SGE_ERR_ARG before any device work.  The first call on each device looks
+ * up that device's copy of the array; make it before capturing a stream.
+ * All calls share the one array, and each call clears the parts that must
+ * start at zero, so calls must not overlap on the GPU: calls that run at
+ * the same time (on different streams or host threads) race and corrupt
+ * each other's results.
+ *
+ * Returns SGE_OK, SGE_ERR_ARG (bad arguments or sizes), SGE_ERR_CUDA, or
+ * SGE_ERR_TIMEOUT (out holds partial counters).  The caller's CSR is not
+ * validated on the device; ids out of range are undefined behaviour. */
+sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_col, const int32_t *d_vlabel,
+                             const int32_t *d_elabel, int32_t k, int64_t m, const int32_t *src, const int32_t *dst,
+                             const int32_t *vlabel, const int32_t *elabel, void *cuda_stream, int64_t time_limit_ms,
+                             uint64_t *out);
+
 /* Ask the running search(es) to stop; they return SGE_ERR_CANCELLED.
  * Callable from any thread. */
 sge_status sge_cancel(sge_ctx *ctx);

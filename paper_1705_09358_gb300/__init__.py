@@ -31,7 +31,7 @@ ERROR_NAMES = {0: "OK", -1: "ARG", -2: "OOM", -3: "CUDA", -4: "BUDGET", -5: "TIM
 # every entry point declared in include/sge.h
 SYMBOLS = ["sge_create", "sge_destroy", "sge_load_target", "sge_load_pattern", "sge_unload_target",
            "sge_unload_pattern", "sge_count", "sge_enumerate", "sge_count_batch", "sge_serve_submit",
-           "sge_serve_poll", "sge_serve_drain", "sge_cancel", "sge_last_error", "sge_version"]
+           "sge_serve_poll", "sge_serve_drain", "sge_cancel", "sge_last_error", "sge_version", "sge_count_noalloc"]
 
 
 class sge_opts(C.Structure):
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
     lib.sge_serve_submit.argtypes = [P, I32, I32, C.POINTER(sge_opts), C.POINTER(I64)]
     lib.sge_serve_poll.argtypes = [P, I64, C.POINTER(I32), C.POINTER(sge_result)]
     lib.sge_serve_drain.argtypes = [P]
+    lib.sge_count_noalloc.argtypes = [I32, P, P, P, P, I32, I64, P, P, P, P, P, I64, P]
     lib.sge_cancel.argtypes = [P]
     lib.sge_last_error.argtypes = [P]
     lib.sge_last_error.restype = C.c_char_p
@@ -237,6 +238,23 @@ def sge_serve_poll(ctx, ticket: int):
 
 def sge_serve_drain(ctx) -> None:
     _check(ctx, load_library().sge_serve_drain(ctx), "sge_serve_drain")
+
+
+def sge_count_noalloc(n, d_rowptr, d_col, d_vlabel, d_elabel, pattern, stream=None, time_limit_ms=0):
+    """Count with no device allocation (see include/sge.h).
+
+    The target arguments are device addresses (ints, e.g. a tensor's
+    ``data_ptr()``; ``d_elabel`` may be 0/None); ``pattern`` has ``n``,
+    ``src``, ``dst``, ``vlabel``, ``elabel`` as host arrays.  Returns
+    (status, dict of the four counters)."""
+    src, dst, vl, el = _i32(pattern.src), _i32(pattern.dst), _i32(pattern.vlabel), _i32(pattern.elabel)
+    out = np.zeros(4, dtype=np.uint64)
+    sp = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    rc = load_library().sge_count_noalloc(int(n), C.c_void_p(int(d_rowptr or 0)), C.c_void_p(int(d_col or 0)),
+                                          C.c_void_p(int(d_vlabel or 0)), C.c_void_p(int(d_elabel or 0)),
+                                          int(pattern.n), int(src.shape[0]), _p(src), _p(dst), _p(vl), _p(el), sp,
+                                          int(time_limit_ms), _p(out))
+    return int(rc), {"matches": int(out[0]), "states": int(out[1]), "nodes": int(out[2]), "hash": int(out[3])}
 
 
 def sge_cancel(ctx) -> None:

@@ -174,14 +174,28 @@ struct TargetRec {
     }
 };
 
+// The host-side facts about a pattern that the ordering and the position
+// tables read: labels, degrees, the k x k arc-label matrix and undirected
+// neighbourhood bitsets (two words per vertex, k <= 128).
+struct PatView {
+    int k;
+    bool directed;
+    const int32_t *lab, *odeg, *ideg;
+    const int *amat;       // k x k, NO_ARC if absent
+    const uint64_t *nb;    // 2 words per vertex
+};
+
 struct PatternRec {
     int k = 0;
     bool directed = false, any_elab = false;
     std::vector<int32_t> lab, odeg, ideg;
     std::vector<int> amat;                 // k x k arc labels, NO_ARC if absent
-    std::vector<std::vector<uint64_t>> nb; // undirected neighbourhood bitsets (2 words, k <= 128)
+    std::vector<uint64_t> nb;              // undirected neighbourhood bitsets (2 words per vertex)
     std::vector<int> ri_mu, ri_par;        // cached RI ordering
     DevBuf dlab, dodeg, dideg, drow, dcol, delab, dirow, dicol, dielab;
+    PatView core() const {
+        return PatView{k, directed, lab.data(), odeg.data(), ideg.data(), amat.data(), nb.data()};
+    }
     PatternView view() const {
         PatternView v;
         v.k = k;
@@ -296,31 +310,31 @@ struct OrderKey {
     long long dsz;
 };
 
-void gcf_order(const PatternRec &P, int algo, const long long *dsize, std::vector<int> &mu, std::vector<int> &par) {
+void gcf_order_into(const PatView &P, int algo, const long long *dsize, int *mu, int *par) {
     const int k = P.k;
     const bool si = algo == SGE_RIDS_SI || algo == SGE_RIDS_SI_FC;
     uint64_t in[2] = {0, 0};
     auto has = [&](const uint64_t *s, int v) { return (s[v >> 6] >> (v & 63)) & 1ull; };
     auto deg = [&](int v) -> long { return P.odeg[v] + (P.directed ? P.ideg[v] : 0); };
-    mu.clear();
+    int len = 0;
     if (algo != SGE_RI)
         for (int v = 0; v < k; ++v)
-            if (dsize[v] == 1) { mu.push_back(v); in[v >> 6] |= 1ull << (v & 63); }
-    if (mu.empty() && k > 0) {
+            if (dsize[v] == 1) { mu[len++] = v; in[v >> 6] |= 1ull << (v & 63); }
+    if (len == 0 && k > 0) {
         int best = 0;
         for (int v = 1; v < k; ++v) {
             const long dv = deg(v), db = deg(best);
             if (dv > db || (dv == db && si && dsize[v] < dsize[best])) best = v;
         }
-        mu.push_back(best);
+        mu[len++] = best;
         in[best >> 6] |= 1ull << (best & 63);
     }
-    while ((int)mu.size() < k) {
+    while (len < k) {
         int best = -1;
         OrderKey bk{0, 0, 0, 0};
         for (int v = 0; v < k; ++v) {
             if (has(in, v)) continue;
-            const uint64_t *nv = P.nb[v].data();
+            const uint64_t *nv = P.nb + 2 * v;
             OrderKey key;
             key.wm = __builtin_popcountll(nv[0] & in[0]) + __builtin_popcountll(nv[1] & in[1]);
             // vertices of mu adjacent to some neighbour x of v outside mu
@@ -330,8 +344,8 @@ void gcf_order(const PatternRec &P, int algo, const long long *dsize, std::vecto
                 while (outside) {
                     const int x = h * 64 + __builtin_ctzll(outside);
                     outside &= outside - 1;
-                    reach[0] |= P.nb[x][0];
-                    reach[1] |= P.nb[x][1];
+                    reach[0] |= P.nb[2 * x];
+                    reach[1] |= P.nb[2 * x + 1];
                 }
             }
             key.wn = __builtin_popcountll(reach[0] & in[0]) + __builtin_popcountll(reach[1] & in[1]);
@@ -346,23 +360,30 @@ void gcf_order(const PatternRec &P, int algo, const long long *dsize, std::vecto
             }
             if (take) { best = v; bk = key; }
         }
-        mu.push_back(best);
+        mu[len++] = best;
         in[best >> 6] |= 1ull << (best & 63);
     }
     // parent: the earliest earlier vertex adjacent to mu_i
-    par.assign(k, -1);
-    for (int i = 0; i < k; ++i)
+    for (int i = 0; i < k; ++i) {
+        par[i] = -1;
         for (int j = 0; j < i; ++j)
-            if (has(P.nb[mu[i]].data(), mu[j])) { par[i] = j; break; }
+            if (has(P.nb + 2 * mu[i], mu[j])) { par[i] = j; break; }
+    }
 }
 
-// Position tables of one search from its ordering (rules 2-4 per position).
-void build_positions(const PatternRec &P, const std::vector<int> &mu, const std::vector<int> &par, int algo,
-                     const long long *dsize, int n, std::vector<PosInfo> &pos, std::vector<BackEdge> &back) {
+void gcf_order(const PatternRec &P, int algo, const long long *dsize, std::vector<int> &mu, std::vector<int> &par) {
+    mu.assign(P.k, -1);
+    par.assign(P.k, -1);
+    gcf_order_into(P.core(), algo, dsize, mu.data(), par.data());
+}
+
+// Position tables of one search from its ordering (rules 2-4 per position),
+// written to caller-provided arrays: pos[k] and back[] (at most k(k-1)/2
+// entries).  Returns the number of back edges.
+int build_positions_into(const PatView &P, const int *mu, const int *par, int algo, const long long *dsize, int n,
+                         PosInfo *pos, BackEdge *back) {
     const int k = P.k;
-    pos.resize(k);
-    std::vector<int> at(k);
-    for (int i = 0; i < k; ++i) at[mu[i]] = i;
+    int nb = 0;
     for (int i = 0; i < k; ++i) {
         const int v = mu[i];
         PosInfo &p = pos[i];
@@ -384,7 +405,7 @@ void build_positions(const PatternRec &P, const std::vector<int> &mu, const std:
         } else {
             p.ucnt = algo == SGE_RI ? n : (int)dsize[v];
         }
-        p.bbeg = (int)back.size();
+        p.bbeg = nb;
         for (int j = 0; j < i; ++j) {
             const int w = mu[j];
             const int lo = P.amat[(size_t)v * k + w], li = P.amat[(size_t)w * k + v];
@@ -395,16 +416,24 @@ void build_positions(const PatternRec &P, const std::vector<int> &mu, const std:
                 if (p.flags & POS_IN_ROW) need_out = false; else need_in = false;
                 if (!need_out && !need_in) continue;
             }
-            BackEdge be;
+            BackEdge &be = back[nb++];
             be.pos = j;
             be.dir = P.directed ? ((need_out ? 1 : 0) | (need_in ? 2 : 0)) : 1;
             be.lab_out = need_out ? lo : 0;
             be.lab_in = need_in ? li : 0;
-            back.push_back(be);
         }
-        p.bcnt = (int)back.size() - p.bbeg;
+        p.bcnt = nb - p.bbeg;
     }
-    (void)at;
+    return nb;
+}
+
+void build_positions(const PatternRec &P, const std::vector<int> &mu, const std::vector<int> &par, int algo,
+                     const long long *dsize, int n, std::vector<PosInfo> &pos, std::vector<BackEdge> &back) {
+    const int k = P.k;
+    pos.resize(k);
+    back.resize((size_t)k * (k > 0 ? k - 1 : 0) / 2 + 1);
+    const int nb = build_positions_into(P.core(), mu.data(), par.data(), algo, dsize, n, pos.data(), back.data());
+    back.resize(nb);
 }
 
 struct Job {
@@ -955,13 +984,13 @@ sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *s
     P->odeg = g.odeg;
     P->ideg = g.ideg;
     P->amat.assign((size_t)n * n, NO_ARC);
-    P->nb.assign(n, std::vector<uint64_t>(2, 0));
+    P->nb.assign(2 * (size_t)n, 0);
     for (int v = 0; v < n; ++v)
         for (int e = g.out.ptr[v]; e < g.out.ptr[v + 1]; ++e) {
             const int w = g.out.col[e];
             P->amat[(size_t)v * n + w] = g.out.lab[e];
-            P->nb[v][w >> 6] |= 1ull << (w & 63);
-            P->nb[w][v >> 6] |= 1ull << (v & 63);
+            P->nb[2 * v + (w >> 6)] |= 1ull << (w & 63);
+            P->nb[2 * w + (v >> 6)] |= 1ull << (v & 63);
         }
     gcf_order(*P, SGE_RI, nullptr, P->ri_mu, P->ri_par);
     CK(upload(P->dlab, g.vlab, st), "upload pattern labels");
@@ -1052,6 +1081,143 @@ sge_status sge_enumerate(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, co
         if (sink(user, rows.data() + i * k, c, k) != 0) return fail(ctx, SGE_ERR_STOPPED, "sink stopped");
     }
     return SGE_OK;
+}
+
+// No device allocation: see include/sge.h.  All host-side work uses fixed
+// arrays on the stack; all device-side data lives in the library's fixed
+// scratch array (sge_noalloc.cu).
+sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_col, const int32_t *d_vlabel,
+                             const int32_t *d_elabel, int32_t k, int64_t m, const int32_t *src, const int32_t *dst,
+                             const int32_t *vlabel, const int32_t *elabel, void *cuda_stream, int64_t time_limit_ms,
+                             uint64_t *out) {
+    if (!out || n < 0 || k < 0 || m < 0) return SGE_ERR_ARG;
+    out[0] = out[1] = out[2] = out[3] = 0;
+    if (k > KMAX) return SGE_ERR_ARG;
+    if (n > 0 && (!d_rowptr || !d_vlabel)) return SGE_ERR_ARG;
+    if (m > 0 && (!src || !dst)) return SGE_ERR_ARG;
+    if (k > 0 && !vlabel) return SGE_ERR_ARG;
+    if (k == 0 || k > n) return SGE_OK;                  // no match and no search
+    // the pattern, validated into fixed arrays
+    int amat[KMAX * KMAX];
+    uint64_t nbits[2 * KMAX];
+    int32_t lab[KMAX], odeg[KMAX];
+    bool any_elab = d_elabel != nullptr;
+    for (int i = 0; i < k * k; ++i) amat[i] = NO_ARC;
+    for (int i = 0; i < 2 * k; ++i) nbits[i] = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        const int a = src[e], b = dst[e], l = elabel ? elabel[e] : 0;
+        if (a < 0 || a >= k || b < 0 || b >= k || a == b) return SGE_ERR_ARG;
+        if (amat[a * k + b] != NO_ARC && amat[a * k + b] != l) return SGE_ERR_ARG;
+        amat[a * k + b] = amat[b * k + a] = l;
+        nbits[2 * a + (b >> 6)] |= 1ull << (b & 63);
+        nbits[2 * b + (a >> 6)] |= 1ull << (a & 63);
+        if (l != 0) any_elab = true;
+    }
+    for (int v = 0; v < k; ++v) {
+        lab[v] = vlabel[v];
+        odeg[v] = __builtin_popcountll(nbits[2 * v]) + __builtin_popcountll(nbits[2 * v + 1]);
+    }
+    const PatView P{k, false, lab, odeg, odeg, amat, nbits};
+    int mu[KMAX], par[KMAX];
+    gcf_order_into(P, SGE_RI, nullptr, mu, par);
+    PosInfo pos[KMAX];
+    BackEdge back[KMAX * (KMAX - 1) / 2 + 1];
+    const int nb = build_positions_into(P, mu, par, SGE_RI, nullptr, n, pos, back);
+
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    void *base = nullptr;
+    size_t cap = 0;
+    if (noalloc_scratch(&base, &cap) != cudaSuccess) return SGE_ERR_CUDA;
+    int32_t nnz = 0;
+    const bool zero_elab = any_elab && d_elabel == nullptr;   // labelled pattern, unlabelled target
+    if (zero_elab && cudaMemcpy(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SGE_ERR_CUDA;
+    // carve the scratch (256-byte aligned pieces)
+    constexpr int POOL = 2048;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return static_cast<unsigned char *>(base) + at;
+    };
+    JobDesc *djob = reinterpret_cast<JobDesc *>(take(sizeof(JobDesc)));
+    unsigned long long *dctr = reinterpret_cast<unsigned long long *>(take(6 * 8));
+    unsigned long long *dctl = reinterpret_cast<unsigned long long *>(take(64 * 8));
+    int32_t *dfront = reinterpret_cast<int32_t *>(take(FRAME_HDR * 4));
+    PosInfo *dpos = reinterpret_cast<PosInfo *>(take((size_t)k * sizeof(PosInfo)));
+    BackEdge *dback = reinterpret_cast<BackEdge *>(take((size_t)(nb > 0 ? nb : 1) * sizeof(BackEdge)));
+    unsigned long long *dseq = reinterpret_cast<unsigned long long *>(take((size_t)POOL * 8));
+    int32_t *dpool = reinterpret_cast<int32_t *>(take((size_t)POOL * POOL_STRIDE * 4));
+    int2 *dvld = reinterpret_cast<int2 *>(take((size_t)n * sizeof(int2)));
+    int32_t *delab = zero_elab ? reinterpret_cast<int32_t *>(take((size_t)nnz * 4)) : nullptr;
+    if (off > cap) return SGE_ERR_ARG;   // target too large for the fixed scratch
+
+    JobDesc D;
+    std::memset(&D, 0, sizeof(D));
+    D.t.n = n;
+    D.t.dw = (n + 63) / 64;
+    D.t.rowptr = D.t.irowptr = d_rowptr;
+    D.t.col = D.t.icol = d_col;
+    D.t.elab = D.t.ielab = zero_elab ? delab : d_elabel;
+    D.t.vld = dvld;
+    D.pos = dpos;
+    D.back = dback;
+    D.k = k;
+    D.flags = any_elab ? JOB_ELAB : 0;
+    D.ctr = dctr;
+    D.mlen = dctr + 4;
+    D.abytes = dctr + 5;
+    const int32_t root[FRAME_HDR] = {0, 0, -1, -1};
+    const int one = 1;
+    int *c32 = reinterpret_cast<int *>(dctl + 8);
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    ok(launch_make_vld(d_rowptr, d_vlabel, dvld, n, st));
+    if (zero_elab) ok(cudaMemsetAsync(delab, 0, (size_t)nnz * 4, st));
+    // every call shares the array: clear what must start at zero
+    ok(cudaMemsetAsync(dctr, 0, 6 * 8, st));
+    ok(cudaMemsetAsync(dctl, 0, 64 * 8, st));
+    ok(cudaMemcpyAsync(djob, &D, sizeof(D), cudaMemcpyHostToDevice, st));
+    ok(cudaMemcpyAsync(dpos, pos, (size_t)k * sizeof(PosInfo), cudaMemcpyHostToDevice, st));
+    if (nb > 0) ok(cudaMemcpyAsync(dback, back, (size_t)nb * sizeof(BackEdge), cudaMemcpyHostToDevice, st));
+    ok(cudaMemcpyAsync(dfront, root, sizeof(root), cudaMemcpyHostToDevice, st));
+    ok(cudaMemcpyAsync(c32, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    ok(launch_pool_init(dseq, POOL, st));
+    if (e != cudaSuccess) return SGE_ERR_CUDA;
+    SearchCtl C;
+    std::memset(&C, 0, sizeof(C));
+    C.front = dfront;
+    C.nfront = 1;
+    C.fstride = FRAME_HDR;
+    C.shard_index = 0;
+    C.shard_count = 1;
+    C.pcap = POOL;
+    C.fnext = dctl + 0;
+    C.pool = dpool;
+    C.pseq = dseq;
+    C.phead = dctl + 1;
+    C.ptail = dctl + 2;
+    C.donations = dctl + 3;
+    C.outstanding = c32 + 0;
+    C.idle = c32 + 1;
+    C.status = c32 + 2;
+    if (time_limit_ms <= 0) {
+        const char *env = std::getenv("SGE_TIME_LIMIT_MS");
+        if (env) time_limit_ms = std::atoll(env);
+    }
+    C.deadline_ns = time_limit_ms > 0 ? (unsigned long long)time_limit_ms * 1000000ull : 0ull;
+    C.donate = 1;
+    C.gran = 2;
+    int grid = 0;
+    ok(launch_search(1, djob, C, k, 1, 0, 0, 0, &grid, st));
+    unsigned long long hc[4] = {0, 0, 0, 0};
+    int status = 0;
+    ok(cudaMemcpyAsync(hc, dctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(&status, C.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ok(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) return SGE_ERR_CUDA;
+    for (int i = 0; i < 4; ++i) out[i] = hc[i];
+    return status;
 }
 
 sge_status sge_cancel(sge_ctx *ctx) {

@@ -157,4 +157,9 @@ size_t search_smem_bytes(int kernel, int kmax, int nwl);
 // Global scratch the search kernel needs for a grid of `grid` blocks.
 size_t search_slab_bytes(int kernel, int kmax, int nwl, long long grid);
 
+// Fixed scratch of sge_count_noalloc (sge_noalloc.cu): the current device's
+// address of the library's static device array, set up once per device.
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
+cudaError_t launch_make_vld(const int32_t *rowptr, const int32_t *vlabel, int2 *vld, int n, cudaStream_t st);
+
 }  // namespace sge
