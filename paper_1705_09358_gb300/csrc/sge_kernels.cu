@@ -838,8 +838,8 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 // adjacency bitset and `used` the images M_0..M_{i-1} (rule 1).  Lane l owns
 // words l, l + 32, ... (NWL per lane).
 //
-// Per warp, shared memory holds the used bitset, M, the hash prefixes, a
-// compact copy of the job's position table, and for every level a list of
+// Per warp, shared memory holds the used bitset, M, a compact copy of the
+// job's position table, and for every level a list of
 // up to LIST_CAP pending survivors; a level with more survivors keeps its
 // bitset in the warp's slab of global scratch (`SearchCtl::slab`) instead.
 
@@ -852,8 +852,7 @@ struct PosB {
 };
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
-    return round16((size_t)(kmax + 1) * 8 +                 // psum
-                   (size_t)nwl * 32 * 8 +                   // used bitset
+    return round16((size_t)nwl * 32 * 8 +                   // used bitset
                    (size_t)kmax * 4 +                       // M
                    (size_t)kmax * sizeof(PosB) +            // position table
                    (size_t)kmax * LIST_CAP * 2 +            // survivor lists
@@ -872,7 +871,6 @@ struct BitsJob {
 };
 
 struct BitsWarp {
-    unsigned long long *psum;
     uint64_t *used;
     int *M;
     PosB *tab;
@@ -888,10 +886,11 @@ __device__ __forceinline__ void used_flip(uint64_t *used, int v) {
     if ((threadIdx.x & 31) == (q & 31)) used[(q >> 5) * 32 + (q & 31)] ^= 1ull << (v & 63);
 }
 
+// Expand position i: compute S_i, count its survivors (the accepted nodes),
+// and either hash them as matches (leaf) or keep them as pending survivors.
 template <int NWL>
-__device__ __forceinline__ unsigned long long bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W, int i,
-                                                          bool leaf, unsigned long long &st, unsigned long long &hs,
-                                                          unsigned long long &ab) {
+__device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W, int i, bool leaf,
+                                           unsigned long long &st, unsigned long long &hs, unsigned long long &ab) {
     const int lane = threadIdx.x & 31;
     const PosB p = W.tab[i];
     const int dw = B.dw;
@@ -931,8 +930,13 @@ __device__ __forceinline__ unsigned long long bits_expand(const BitsJob &B, cons
         s[w] &= ~W.used[w * 32 + lane];
         cnt += __popcll(s[w]);
     }
+    const int total = __reduce_add_sync(FULL, (unsigned)cnt);
     if (leaf) {
-        const unsigned long long psum_i = W.psum[i];
+        if (total == 0) return 0;
+        // hash prefix sum_{t < i} g(mu_t, M_t), computed only when matches exist
+        unsigned long long ps = 0;
+        for (int t = lane; t < i; t += 32) ps += gterm(W.tab[t].pv, M[t]);
+        ps = warp_sum(ps);
 #pragma unroll
         for (int w = 0; w < NWL; ++w) {
             const int q = lane + 32 * w;
@@ -940,22 +944,27 @@ __device__ __forceinline__ unsigned long long bits_expand(const BitsJob &B, cons
             while (y) {
                 const int bit = __ffsll((long long)y) - 1;
                 const int vtx = q * 64 + bit;
-                hs += fmix64(psum_i + gterm(p.pv, vtx));
+                hs += fmix64(ps + gterm(p.pv, vtx));
                 if (J.mbuf) emit_match(J, M, i, vtx);
                 y &= y - 1;
             }
         }
-        return warp_sum((unsigned long long)cnt);
+        return total;
     }
     // pending survivors: a short list in shared memory, else the bitset in the slab
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
+    if (total == 0) {
+        __syncwarp();
+        if (lane == 0) W.lcnt[i] = 0;
+        __syncwarp();
+        return 0;
     }
-    const int total = __shfl_sync(FULL, incl, 31);
     if (total <= LIST_CAP) {
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
         uint16_t *L = W.lst + i * LIST_CAP;
         int o = incl - cnt;
 #pragma unroll
@@ -967,15 +976,17 @@ __device__ __forceinline__ unsigned long long bits_expand(const BitsJob &B, cons
                 y &= y - 1;
             }
         }
+        __syncwarp();
         if (lane == 0) W.lcnt[i] = (uint8_t)total;
     } else {
         uint64_t *Sl = W.slab + (size_t)i * NWL * 32;
 #pragma unroll
         for (int w = 0; w < NWL; ++w) Sl[w * 32 + lane] = s[w];
+        __syncwarp();
         if (lane == 0) W.lcnt[i] = LIST_SPILLED;
     }
     __syncwarp();
-    return (unsigned long long)total;
+    return total;
 }
 
 // Next pending survivor of level l (warp-uniform, -1 if none); removes it.
@@ -1030,8 +1041,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
     BitsWarp W;
-    W.psum = reinterpret_cast<unsigned long long *>(base);
-    W.used = reinterpret_cast<uint64_t *>(W.psum + kmax + 1);
+    W.used = reinterpret_cast<uint64_t *>(base);
     W.M = reinterpret_cast<int *>(W.used + NWL * 32);
     W.tab = reinterpret_cast<PosB *>(W.M + kmax);
     W.lst = reinterpret_cast<uint16_t *>(W.tab + kmax);
@@ -1066,19 +1076,16 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         const int k = B.k, d0 = fr.depth;
         unsigned long long st = 0, nd = 0, mt = 0, hs = 0, ab = 0;
         {
-            unsigned long long s = 0;
-            for (int t = lane; t < d0; t += 32) s += gterm(W.tab[t].pv, M[t]);
-            s = warp_sum(s);
 #pragma unroll
             for (int w = 0; w < NWL; ++w) W.used[w * 32 + lane] = 0ull;
             __syncwarp();
             for (int t = 0; t < d0; ++t) used_flip<NWL>(W.used, M[t]);
-            if (lane == 0) { W.psum[d0] = s; M[d0] = -1; }
+            if (lane == 0) M[d0] = -1;
             __syncwarp();
         }
         bool stopped = false;
         if (d0 == k - 1) {
-            const unsigned long long c = bits_expand<NWL>(B, J, W, d0, true, st, hs, ab);
+            const int c = bits_expand<NWL>(B, J, W, d0, true, st, hs, ab);
             nd += c; mt += c;
         } else {
             nd += bits_expand<NWL>(B, J, W, d0, false, st, hs, ab);
@@ -1120,13 +1127,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     continue;
                 }
                 used_flip<NWL>(W.used, v);
-                if (lane == 0) {
-                    M[lvl] = v;
-                    W.psum[lvl + 1] = W.psum[lvl] + gterm(W.tab[lvl].pv, v);
-                }
+                if (lane == 0) M[lvl] = v;
                 __syncwarp();
                 if (lvl + 1 == k - 1) {
-                    const unsigned long long c = bits_expand<NWL>(B, J, W, lvl + 1, true, st, hs, ab);
+                    const int c = bits_expand<NWL>(B, J, W, lvl + 1, true, st, hs, ab);
                     nd += c; mt += c;
                 } else {
                     nd += bits_expand<NWL>(B, J, W, lvl + 1, false, st, hs, ab);
