@@ -104,6 +104,7 @@ typedef struct {
                                 CSR kernel: 12 per state (4-byte candidate id + 8-byte
                                 label/degree record) */
     int64_t launches;        /* CUDA kernels this call launched */
+    double latency_ms;       /* serving: from sge_serve_submit to completion (host clock) */
     int32_t split_depth;     /* depth of that frontier */
     int32_t status;          /* SGE_OK or the error of this pair */
     int32_t kernel;          /* SGE_KERNEL_CSR or SGE_KERNEL_BITSET as used */
@@ -168,9 +169,11 @@ sge_status sge_count_batch(sge_ctx *ctx, int64_t npairs, const int32_t *target_i
                            const int32_t *pattern_ids, const sge_opts *opts, sge_result *out);
 
 /* Serving (continuous batching).  sge_serve_submit queues one query and
- * returns at once with a ticket; a scheduler thread owned by the context
- * admits queued queries into free device slots as memory allows, launching
- * each admitted group while earlier groups still run on other streams.
+ * returns at once with a ticket; scheduler threads owned by the context
+ * admit queued queries into free launch slots as memory allows, each slot
+ * launching its admitted group on its own stream with half of the GPU's
+ * resident blocks (unless opts->blocks_per_sm says otherwise), so groups
+ * overlap on the device while earlier ones still run.
  * sge_serve_poll sets *done = 1 and fills *out once the query finished
  * (out->status holds its own error), else *done = 0.  Errors: ARG,
  * NOT_FOUND. */

@@ -45,7 +45,7 @@ class sge_result(C.Structure):
     _fields_ = [("matches", C.c_uint64), ("states", C.c_uint64), ("nodes", C.c_uint64), ("hash", C.c_uint64),
                 ("preprocess_ms", C.c_double), ("match_ms", C.c_double), ("search_kernel_ms", C.c_double),
                 ("frames", C.c_int64), ("donations", C.c_int64), ("alg_bytes", C.c_uint64),
-                ("launches", C.c_int64), ("split_depth", C.c_int32),
+                ("launches", C.c_int64), ("latency_ms", C.c_double), ("split_depth", C.c_int32),
                 ("status", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
@@ -116,6 +116,7 @@ def result_dict(r: sge_result) -> dict:
             "preprocess_ms": float(r.preprocess_ms), "match_ms": float(r.match_ms),
             "search_kernel_ms": float(r.search_kernel_ms), "frames": int(r.frames),
             "donations": int(r.donations), "alg_bytes": int(r.alg_bytes), "launches": int(r.launches),
+            "latency_ms": float(r.latency_ms),
             "split_depth": int(r.split_depth), "status": int(r.status),
             "kernel": int(r.kernel)}
 

@@ -270,6 +270,7 @@ struct ServeReq {
     sge_result res;
     bool done = false;
     long long bytes = 0;
+    double t_submit = 0;
 };
 
 sge_status fail(sge_ctx *ctx, sge_status code, const std::string &msg) {
@@ -599,34 +600,44 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                     if (s == 0) J.active = false;   // an empty domain: no match, no search
         }
     }
-    // orderings and position tables
+    // orderings and position tables; RI tables depend only on the pattern and
+    // are shared by every job of that pattern (n_t of an unparented RI position
+    // is read from the job's target at run time)
     std::vector<PosInfo> pos;
     std::vector<BackEdge> back;
     std::vector<long long> pos_off(nj, 0), back_off(nj, 0);
     std::vector<int> task_job, task_vert, task_out;
+    std::vector<int> fidx(nj, -1);
+    for (int x = 0; x < nf; ++x) fidx[fjobs[x]] = x;
+    std::map<const PatternRec *, std::pair<long long, long long>> ri_tables;
     long long ulist_len = 0;
+    std::vector<PosInfo> pq;
+    std::vector<BackEdge> bq;
     for (int q = 0; q < nj; ++q) {
         Job &J = jobs[q];
         if (!J.active) continue;
         if (J.algo == SGE_RI) {
-            J.mu = J.p->ri_mu;
-            J.par = J.p->ri_par;
-        } else {
-            gcf_order(*J.p, J.algo, J.dsize.data(), J.mu, J.par);
+            auto it = ri_tables.find(J.p);
+            if (it == ri_tables.end()) {
+                const long long po = (long long)pos.size(), bo = (long long)back.size();
+                build_positions(*J.p, J.p->ri_mu, J.p->ri_par, SGE_RI, nullptr, 0, pq, bq);
+                pos.insert(pos.end(), pq.begin(), pq.end());
+                back.insert(back.end(), bq.begin(), bq.end());
+                it = ri_tables.emplace(J.p, std::make_pair(po, bo)).first;
+            }
+            pos_off[q] = it->second.first;
+            back_off[q] = it->second.second;
+            continue;
         }
+        gcf_order(*J.p, J.algo, J.dsize.data(), J.mu, J.par);
         pos_off[q] = (long long)pos.size();
         back_off[q] = (long long)back.size();
-        std::vector<PosInfo> pq;
-        std::vector<BackEdge> bq;
-        build_positions(*J.p, J.mu, J.par, J.algo, J.dsize.empty() ? nullptr : J.dsize.data(), J.t->n, pq, bq);
+        build_positions(*J.p, J.mu, J.par, J.algo, J.dsize.data(), J.t->n, pq, bq);
         for (PosInfo &p : pq) {
-            if (p.par < 0 && J.algo != SGE_RI) {
-                p.uoff = (int)ulist_len;
+            if (p.par < 0) {
                 // the D(mu_i) list is written by a kernel below
-                int fq = -1;
-                for (int x = 0; x < nf; ++x)
-                    if (fjobs[x] == q) { fq = x; break; }
-                task_job.push_back(fq);
+                p.uoff = (int)ulist_len;
+                task_job.push_back(fidx[q]);
                 task_vert.push_back(p.pv);
                 task_out.push_back((int)ulist_len);
                 ulist_len += p.ucnt;
@@ -1274,11 +1285,19 @@ void serve_worker(sge_ctx *ctx) {
         std::vector<PairReq> reqs;
         for (auto &r : group) reqs.push_back({r->tid, r->pid});
         std::vector<sge_result> res(group.size());
-        sge_status rc = run_pairs(ctx, W, st, reqs, &group[0]->opts, res.data(), false, nullptr, 0);
+        sge_opts o = group[0]->opts;
+        if (o.blocks_per_sm <= 0) {
+            // half of the resident blocks per group, so concurrent groups overlap on the device
+            int occ = 0;
+            if (search_blocks_per_sm(1, KMAX, 1, 0, &occ) == cudaSuccess && occ > 1) o.blocks_per_sm = occ / 2;
+        }
+        sge_status rc = run_pairs(ctx, W, st, reqs, &o, res.data(), false, nullptr, 0);
+        const double t_done = now_ms();
         {
             std::lock_guard<std::mutex> lk(ctx->smu);
             for (size_t i = 0; i < group.size(); ++i) {
                 group[i]->res = res[i];
+                group[i]->res.latency_ms = t_done - group[i]->t_submit;
                 if (rc != SGE_OK && res[i].status == 0) group[i]->res.status = rc;
                 group[i]->done = true;
             }
@@ -1304,6 +1323,7 @@ sge_status sge_serve_submit(sge_ctx *ctx, int32_t target_id, int32_t pattern_id,
     std::memset(&r->opts, 0, sizeof(sge_opts));
     if (opts) r->opts = *opts;
     std::memset(&r->res, 0, sizeof(r->res));
+    r->t_submit = now_ms();
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         auto ti = ctx->targets.find(target_id);

@@ -43,7 +43,7 @@ struct PosInfo {
     int32_t pel;    // label of the pattern arc joining mu_i and P(mu_i) along the row used
     int32_t bbeg;   // back edges [bbeg, bbeg + bcnt) in the job's BackEdge array
     int32_t bcnt;
-    int32_t ucnt;   // unparented: number of raw candidates (n_t for RI, |D(mu_i)| for RI-DS)
+    int32_t ucnt;   // unparented RI-DS: |D(mu_i)| raw candidates (RI reads n_t from the target)
     int32_t uoff;   // unparented RI-DS: offset of D(mu_i) in the job's candidate list
     int32_t flags;  // POS_IN_ROW
     int32_t pad;

@@ -676,20 +676,81 @@ __device__ __forceinline__ bool donation_wanted(const SearchCtl &C) {
 }
 
 // ===================================================== search: CSR kernel
-
-struct LvCsr {
-    const int32_t *ptr;  // candidate array (null = identity)
-    long long base;      // offset of the candidate list in ptr
-    int cur, end;        // unscanned candidates [cur, end)
-    unsigned mask;       // survivors of the last scanned chunk, not yet descended
-    int cbase;           // index of that chunk's first candidate
-};
+//
+// One warp owns one depth-first search.  A level's candidates are the row of
+// M(P(mu_i)) (or V_t / D(mu_i) when mu_i is unparented), scanned 32 at a time,
+// one candidate per lane; each lane tests rules 1-4 and the domain bit, and a
+// ballot compacts the chunk's survivors.  Per warp, shared memory holds M,
+// the level records and a compact copy of the job's position table; the
+// job's pointers stay in registers.
 
 __host__ __device__ __forceinline__ size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+struct PosC {                // hot fields of one position
+    int16_t pv, par, bb, bc;
+    int32_t lab, odeg, ideg, pel, flags;
+};
+
+struct LvCsr {
+    int base;                // offset of the level's candidate list in its array
+    int cur, end;            // unscanned candidates [cur, end)
+    unsigned mask;           // survivors of the last scanned chunk, not yet descended
+    int cbase;               // index of that chunk's first candidate
+};
+
 __host__ __device__ __forceinline__ size_t csr_smem_per_warp(int kmax) {
-    return round16((size_t)(kmax + 1) * sizeof(unsigned long long) + (size_t)kmax * sizeof(LvCsr) +
-                   (size_t)kmax * sizeof(int));
+    return round16((size_t)kmax * sizeof(LvCsr) + (size_t)kmax * sizeof(int) + (size_t)kmax * sizeof(PosC));
+}
+
+struct CsrJob {
+    const int32_t *rowptr, *col, *elab, *irowptr, *icol, *ielab, *indeg, *ulist;
+    const int2 *vld;
+    const uint64_t *filt, *adj;
+    const BackEdge *back;
+    int n, dw, k, flags;
+};
+
+// Candidate array of a position: the parent's out- or in-row, D(mu_i), or
+// null for "candidate j is vertex j".
+__device__ __forceinline__ const int32_t *csr_src(const CsrJob &B, const PosC &p) {
+    if (p.par >= 0) return (p.flags & POS_IN_ROW) ? B.icol : B.col;
+    return (B.flags & JOB_RIDS) ? B.ulist : nullptr;
+}
+
+// Rules 1-4 (Section "RI") and the RI-DS domain test for candidate c of
+// position i; eidx is c's index in the parent's row (parent-arc label) or -1.
+template <bool DIR>
+__device__ __forceinline__ bool csr_feasible(const CsrJob &B, const PosC &p, int i, int c, int eidx, const int *M) {
+    const int2 v = __ldg(B.vld + c);
+    if (v.x != p.lab || v.y < p.odeg) return false;                           // rules 2, 3
+    if (DIR && __ldg(B.indeg + c) < p.ideg) return false;                    // rule 3 (in)
+    if (B.flags & JOB_RIDS) {                                                 // v_t in D(mu_i)
+        const uint64_t w = B.filt[(size_t)p.pv * B.dw + (c >> 6)];
+        if (!((w >> (c & 63)) & 1ull)) return false;
+    }
+    const bool chk = (B.flags & JOB_ELAB) != 0;
+    if (chk && eidx >= 0) {                                                   // parent arc label
+        const int l = (p.flags & POS_IN_ROW) ? __ldg(B.ielab + eidx) : __ldg(B.elab + eidx);
+        if (l != p.pel) return false;
+    }
+    for (int b = 0; b < p.bc; ++b) {                                          // rule 4
+        const BackEdge be = B.back[p.bb + b];
+        const int x = M[be.pos];
+        if (!DIR) {
+            if (B.adj != nullptr && !chk) {
+                const uint64_t w = __ldg(B.adj + (size_t)x * B.dw + (c >> 6));
+                if (!((w >> (c & 63)) & 1ull)) return false;
+            } else if (!row_has(B.rowptr, B.col, B.elab, x, c, be.lab_out, chk)) {
+                return false;
+            }
+        } else {
+            if ((be.dir & 1) && !row_has(B.irowptr, B.icol, B.ielab, x, c, be.lab_out, chk)) return false;
+            if ((be.dir & 2) && !row_has(B.rowptr, B.col, B.elab, x, c, be.lab_in, chk)) return false;
+        }
+    }
+    for (int j = 0; j < i; ++j)                                               // rule 1
+        if (M[j] == c) return false;
+    return true;
 }
 
 template <bool DIR>
@@ -697,32 +758,61 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + wib * csr_smem_per_warp(kmax);
-    unsigned long long *psum = reinterpret_cast<unsigned long long *>(base);
-    LvCsr *lv = reinterpret_cast<LvCsr *>(psum + kmax + 1);
+    LvCsr *lv = reinterpret_cast<LvCsr *>(base);
     int *M = reinterpret_cast<int *>(lv + kmax);
+    PosC *tab = reinterpret_cast<PosC *>(M + kmax);
 
-    // the time limit counts from this warp's start on the device clock
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
     long long iter = 0, quiet_until = 0;
+    int cur_job = -1;
+    CsrJob B;
     while (acquire_frame(C, M, fr, deadline)) {
         const JobDesc &J = jobs[fr.job];
-        const int k = J.k, d0 = fr.depth;
-        unsigned long long st = 0, nd = 0, mt = 0, hs = 0;
-        {
-            unsigned long long s = 0;
-            for (int t = lane; t < d0; t += 32) s += gterm(J.pos[t].pv, M[t]);
-            s = warp_sum(s);
-            if (lane == 0) psum[d0] = s;
-        }
-        {
-            const PosInfo P = J.pos[d0];
-            const Src S = cand_source(J, P, M);
-            int cur = 0, end = S.len;
-            if (fr.beg >= 0) { cur = fr.beg; end = min(fr.end, S.len); }
-            else st += (unsigned long long)S.len;
-            if (lane == 0) { lv[d0].ptr = S.ptr; lv[d0].base = S.base; lv[d0].cur = cur; lv[d0].end = end; lv[d0].mask = 0; lv[d0].cbase = 0; }
+        if (fr.job != cur_job) {
+            cur_job = fr.job;
+            B.rowptr = J.t.rowptr; B.col = J.t.col; B.elab = J.t.elab;
+            B.irowptr = J.t.irowptr; B.icol = J.t.icol; B.ielab = J.t.ielab; B.indeg = J.t.indeg;
+            B.ulist = J.ulist; B.vld = J.t.vld; B.filt = J.filt; B.adj = J.t.adj; B.back = J.back;
+            B.n = J.t.n; B.dw = J.t.dw; B.k = J.k; B.flags = J.flags;
+            for (int t = lane; t < B.k; t += 32) {
+                const PosInfo P = J.pos[t];
+                PosC q;
+                q.pv = (int16_t)P.pv; q.par = (int16_t)P.par; q.bb = (int16_t)P.bbeg; q.bc = (int16_t)P.bcnt;
+                q.lab = P.lab; q.odeg = P.odeg; q.ideg = P.ideg; q.pel = P.pel; q.flags = P.flags;
+                tab[t] = q;
+            }
             __syncwarp();
+        }
+        const int k = B.k, d0 = fr.depth;
+        unsigned long long st = 0, nd = 0, mt = 0, hs = 0;
+        // set up level `lvl` (positions 0..lvl-1 assigned); returns the raw candidate count
+        auto setup = [&](int l, int beg, int endv) -> int {
+            const PosC p = tab[l];
+            int b0, len;
+            if (p.par >= 0) {
+                const int a = M[p.par];
+                const int32_t *rp = (p.flags & POS_IN_ROW) ? B.irowptr : B.rowptr;
+                b0 = __ldg(rp + a);
+                len = __ldg(rp + a + 1) - b0;
+            } else if (B.flags & JOB_RIDS) {
+                const PosInfo &P = J.pos[l];
+                b0 = P.uoff;
+                len = P.ucnt;
+            } else {
+                b0 = 0;
+                len = B.n;
+            }
+            int cur = 0, end = len;
+            if (beg >= 0) { cur = beg; end = min(endv, len); }
+            __syncwarp();
+            if (lane == 0) { lv[l].base = b0; lv[l].cur = cur; lv[l].end = end; lv[l].mask = 0; lv[l].cbase = 0; }
+            __syncwarp();
+            return len;
+        };
+        {
+            const int len = setup(d0, fr.beg, fr.end);
+            if (fr.beg < 0) st += (unsigned long long)len;
         }
         int lvl = d0;
         bool stopped = false;
@@ -750,11 +840,12 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                             break;
                         }
                         if (L.mask != 0) {
+                            const int32_t *src = csr_src(B, tab[l]);
                             int given = 0;
                             while (L.mask != 0 && given < C.gran) {
                                 const unsigned m = L.mask;
                                 const int b = __ffs(m) - 1;
-                                const int c = L.ptr ? __ldg(L.ptr + L.base + L.cbase + b) : L.cbase + b;
+                                const int c = src ? __ldg(src + L.base + L.cbase + b) : L.cbase + b;
                                 if (!push_frame(C, fr.job, l + 1, -1, -1, M, l, c)) break;
                                 __syncwarp();
                                 if (lane == 0) L.mask = m & (m - 1);
@@ -768,6 +859,8 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             }
             LvCsr &L = lv[lvl];
             const unsigned mask = L.mask;
+            const PosC p = tab[lvl];
+            const int32_t *src = csr_src(B, p);
             if (mask == 0) {
                 const int cur = L.cur, end = L.end;
                 if (cur >= end) {
@@ -776,21 +869,26 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                     continue;
                 }
                 const int cnt = min(32, end - cur);
-                const PosInfo P = J.pos[lvl];
                 bool ok = false;
                 int c = -1;
                 if (lane < cnt) {
-                    const long long e = L.base + cur + lane;
-                    c = L.ptr ? __ldg(L.ptr + e) : cur + lane;
-                    ok = feasible<DIR>(J, P, lvl, c, (L.ptr && P.par >= 0) ? e : -1, M);
+                    const int e = L.base + cur + lane;
+                    c = src ? __ldg(src + e) : cur + lane;
+                    ok = csr_feasible<DIR>(B, p, lvl, c, (src && p.par >= 0) ? e : -1, M);
                 }
                 unsigned bal = __ballot_sync(FULL, ok);
                 nd += __popc(bal);
                 if (lvl == k - 1) {
                     mt += __popc(bal);
-                    if (ok) {
-                        hs += fmix64(psum[lvl] + gterm(P.pv, c));
-                        if (J.mbuf) emit_match(J, M, lvl, c);
+                    if (bal) {
+                        // hash prefix sum_{t < lvl} g(mu_t, M_t), only when this chunk has matches
+                        unsigned long long ps = 0;
+                        for (int t = lane; t < lvl; t += 32) ps += gterm(tab[t].pv, M[t]);
+                        ps = warp_sum(ps);
+                        if (ok) {
+                            hs += fmix64(ps + gterm(p.pv, c));
+                            if (J.mbuf) emit_match(J, M, lvl, c);
+                        }
                     }
                     bal = 0;
                 }
@@ -801,21 +899,15 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             }
             // descend into the lowest pending survivor
             const int b = __ffs(mask) - 1;
-            const int c = L.ptr ? __ldg(L.ptr + L.base + L.cbase + b) : L.cbase + b;
-            const int pv = J.pos[lvl].pv;
+            const int c = src ? __ldg(src + L.base + L.cbase + b) : L.cbase + b;
             __syncwarp();
             if (lane == 0) {
                 L.mask = mask & (mask - 1);
                 M[lvl] = c;
-                psum[lvl + 1] = psum[lvl] + gterm(pv, c);
             }
             __syncwarp();
             ++lvl;
-            const PosInfo Q = J.pos[lvl];
-            const Src S = cand_source(J, Q, M);
-            st += (unsigned long long)S.len;
-            if (lane == 0) { lv[lvl].ptr = S.ptr; lv[lvl].base = S.base; lv[lvl].cur = 0; lv[lvl].end = S.len; lv[lvl].mask = 0; lv[lvl].cbase = 0; }
-            __syncwarp();
+            st += (unsigned long long)setup(lvl, -1, 0);
         }
         hs = warp_sum(hs);
         if (lane == 0) {
@@ -1065,7 +1157,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                 const PosInfo P = J.pos[t];
                 PosB q;
                 q.pv = (int16_t)P.pv; q.par = (int16_t)P.par; q.bb = (int16_t)P.bbeg; q.bc = (int16_t)P.bcnt;
-                q.ucnt = P.ucnt;
+                q.ucnt = (J.flags & JOB_RIDS) ? P.ucnt : J.t.n;   // RI: all of V_t
                 W.tab[t] = q;
             }
             __syncwarp();
