@@ -78,7 +78,10 @@ typedef struct {
     int32_t shard_index;       /* multi-device form: this device's shard ... */
     int32_t shard_count;       /* ... of the split frontier (0 or 1 = unsharded) */
     int32_t no_donation;       /* 1 = persistent kernel without work donation */
-    int32_t reserved[5];
+    int32_t donate_every_iters;/* a warp donates at most once per this many search iterations ... */
+    int32_t donate_every_us;   /* ... or once per this many microseconds, whichever comes first
+                                  (defaults: CSR kernel 1024 / 500, bitset kernel 2^30 / 2000) */
+    int32_t reserved[3];
 } sge_opts;
 
 /* Result of one (target, pattern) search.
@@ -170,10 +173,10 @@ sge_status sge_count_batch(sge_ctx *ctx, int64_t npairs, const int32_t *target_i
 
 /* Serving (continuous batching).  sge_serve_submit queues one query and
  * returns at once with a ticket; scheduler threads owned by the context
- * admit queued queries into free launch slots as memory allows, each slot
- * launching its admitted group on its own stream with half of the GPU's
- * resident blocks (unless opts->blocks_per_sm says otherwise), so groups
- * overlap on the device while earlier ones still run.
+ * admit every queued query (up to 512, within a device-memory budget) into
+ * the next free launch slot, and each slot runs its admitted group through
+ * the batched launch sequence on its own stream, so a group's host work and
+ * launches overlap with earlier groups still on the device.
  * sge_serve_poll sets *done = 1 and fills *out once the query finished
  * (out->status holds its own error), else *done = 0.  Errors: ARG,
  * NOT_FOUND. */

@@ -10,6 +10,7 @@
 #include "sge_internal.h"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <climits>
@@ -32,12 +33,15 @@ namespace {
 
 constexpr int NO_ARC = INT_MIN;
 constexpr int BITSET_MAX_N = 16384;              // adjacency bitset kept for n <= this (<= 32 MB)
+constexpr int HUB_MIN_DEGREE = 24;               // larger targets: bitset rows for vertices of this degree+
+constexpr long long HUB_BYTES = 512ll << 20;     // ... within this much device memory
 constexpr long long FRONTIER_MAX_INTS = 1ll << 27;  // 512 MB per frontier buffer
 constexpr int POOL_CELLS = 1 << 15;
+constexpr int ROOT_CHUNK = 1024;                 // root candidates per root range frame
 
 // Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
 bool trace_on() {
-    static const bool on = std::getenv("SGE_TRACE") != nullptr;
+    static const bool on = std::getenv("SGE_TRACE") != nullptr && std::getenv("SGE_TRACE")[0] != '0';
     return on;
 }
 
@@ -152,7 +156,7 @@ struct TargetRec {
     int n = 0, dw = 0;
     bool directed = false, any_elab = false;
     long long nnz = 0;
-    DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj;
+    DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj, hub_slot, hub_bits, hub_list;
     TargetView view() const {
         TargetView v;
         v.n = n;
@@ -167,10 +171,14 @@ struct TargetRec {
         v.vld = vld.as<int2>();
         v.indeg = directed ? indeg.as<int32_t>() : nullptr;
         v.adj = adj.p ? adj.as<uint64_t>() : nullptr;
+        v.hub_slot = hub_slot.p ? hub_slot.as<int32_t>() : nullptr;
+        v.hub_bits = hub_bits.p ? hub_bits.as<uint64_t>() : nullptr;
         return v;
     }
     void release() {
-        for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj}) b->release();
+        for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
+                          &hub_list})
+            b->release();
     }
 };
 
@@ -219,13 +227,13 @@ struct PatternRec {
 // Scratch of one launch sequence (the serving scheduler has one per slot).
 struct Workspace {
     DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag;
-    DevBuf front[2], counts, offs, scan_tmp, total;
+    DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
     DevBuf mbuf;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void release() {
         for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
-                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &pool, &pseq, &ctl, &slab, &mbuf})
+                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf})
             b->release();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -692,42 +700,100 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     const long long resident_warps = (long long)ctx->sms * occ * search_warps_per_block();
     const long long fpw = o.frames_per_warp > 0 ? o.frames_per_warp : 32;
     const long long target_frames = fpw * resident_warps * shard_count;
-    std::vector<int32_t> f0;
-    for (int q = 0; q < nj; ++q)
-        if (jobs[q].active) { f0.push_back(q); f0.push_back(0); f0.push_back(-1); f0.push_back(-1); }
-    long long F = (long long)f0.size() / FRAME_HDR;
-    int cur = 0, depth = 0;
-    if (F > 0) CK(upload(W.front[0], f0, st), "upload roots");
-    while (F > 0) {
-        if (o.split_depth > 0) {
-            if (depth >= o.split_depth) break;
-        } else if (F >= target_frames) {
-            break;
+    // roots: one frame per active job, cut into ranges of ROOT_CHUNK candidates
+    // when the root has more (a range frame counts the node's states only if it
+    // starts at candidate 0)
+    std::vector<std::array<int32_t, 4>> roots;
+    for (int q = 0; q < nj; ++q) {
+        const Job &J = jobs[q];
+        if (!J.active) continue;
+        const long long len = J.algo == SGE_RI ? J.t->n : pos[pos_off[q]].ucnt;
+        if (len <= ROOT_CHUNK) {
+            roots.push_back({q, 0, -1, -1});
+        } else {
+            for (long long b = 0; b < len; b += ROOT_CHUNK)
+                roots.push_back({q, 0, (int32_t)b, (int32_t)std::min<long long>(b + ROOT_CHUNK, len)});
         }
-        if (depth >= kmax - 1) break;   // leave the last position to the search kernel
-        CK(W.counts.ensure((size_t)F * 4), "alloc counts");
-        CK(W.offs.ensure((size_t)F * 8), "alloc offsets");
-        CK(W.scan_tmp.ensure(scan_tmp_bytes(F)), "alloc scan");
-        CK(W.total.ensure(16), "alloc total");
-        CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(), nullptr,
-                        nullptr, 0, count_ctr, directed ? 1 : 0, st), "split count");
-        launches += 4;   // split count + three scan kernels
-        CK(launch_scan(W.counts.as<int32_t>(), W.offs.as<long long>(), F, W.total.as<long long>(), W.scan_tmp.p,
-                       W.scan_tmp.cap, st), "split scan");
-        long long total = 0;
-        CK(cudaMemcpyAsync(&total, W.total.p, 8, cudaMemcpyDeviceToHost, st), "read split total");
-        CK(cudaStreamSynchronize(st), "split sync");
-        const long long need = total * (FRAME_HDR + depth + 1);
-        if (need > FRONTIER_MAX_INTS) break;   // keep the current frontier
-        CK(W.front[cur ^ 1].ensure((size_t)std::max<long long>(need, 1) * 4), "alloc frontier");
-        CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(),
-                        W.offs.as<long long>(), W.front[cur ^ 1].as<int32_t>(), 1, count_ctr, directed ? 1 : 0, st),
-           "split write");
-        ++launches;
-        cur ^= 1;
-        F = total;
-        ++depth;
-        if (trace_on()) std::fprintf(stderr, "[sge] split depth %d frames %lld at %.3f ms\n", depth, F, now_ms() - t_start);
+    }
+    const long long F0 = (long long)roots.size();
+    long long F = 0;
+    int cur = 0, depth = 0, fstride = FRAME_HDR;
+    bool split_done = F0 == 0;
+    const int max_levels = std::max(0, std::min(o.split_depth > 0 ? o.split_depth : INT_MAX, kmax - 1));
+    if (!split_done) {
+        // the whole split as one cooperative launch; frames of stride FRAME_HDR + kmax
+        fstride = FRAME_HDR + kmax;
+        const long long target = o.split_depth > 0 ? LLONG_MAX : target_frames;
+        const long long cap =
+            std::max<long long>(F0, std::min<long long>(FRONTIER_MAX_INTS / fstride, 8 * target_frames + F0));
+        CK(W.front[0].ensure((size_t)cap * fstride * 4), "alloc frontier");
+        CK(W.front[1].ensure((size_t)cap * fstride * 4), "alloc frontier");
+        CK(cudaMemcpy2DAsync(W.front[0].p, (size_t)fstride * 4, roots.data(), sizeof(roots[0]), sizeof(roots[0]),
+                             (size_t)F0, cudaMemcpyHostToDevice, st), "upload roots");
+        const long long wcap = (long long)ctx->sms * 32 * search_warps_per_block();
+        const size_t ctl_words = (size_t)wcap + 16;
+        CK(W.splitctl.ensure(ctl_words * 8), "alloc split control");
+        CK(cudaMemsetAsync(W.splitctl.p, 0, ctl_words * 8, st), "clear split control");
+        long long *wtot = W.splitctl.as<long long>();
+        unsigned *bar = reinterpret_cast<unsigned *>(wtot + wcap);
+        long long *res = wtot + wcap + 1;
+        int *sstat = reinterpret_cast<int *>(res + 4);
+        const cudaError_t le = launch_split_coop(W.jobs.as<JobDesc>(), F0, W.front[0].as<int32_t>(),
+                                                 W.front[1].as<int32_t>(), fstride, cap, target, max_levels, wtot,
+                                                 wcap, bar, res, sstat, count_ctr, directed ? 1 : 0, st);
+        if (le == cudaSuccess) {
+            ++launches;
+            long long r4[4] = {0, 0, 0, 0};
+            int ss = 0;
+            CK(cudaMemcpyAsync(r4, res, sizeof(r4), cudaMemcpyDeviceToHost, st), "read split result");
+            CK(cudaMemcpyAsync(&ss, sstat, sizeof(int), cudaMemcpyDeviceToHost, st), "read split status");
+            CK(cudaStreamSynchronize(st), "split sync");
+            if (ss != 0) return fail(ctx, SGE_ERR_CUDA, "device split barrier timed out");
+            F = r4[0];
+            cur = (int)r4[1];
+            depth = (int)r4[2];
+            split_done = true;
+            if (trace_on())
+                std::fprintf(stderr, "[sge] device split: %d levels, %lld frames at %.3f ms\n", depth, F,
+                             now_ms() - t_start);
+        } else {
+            (void)cudaGetLastError();   // cooperative launch refused: split level by level below
+        }
+    }
+    if (!split_done) {
+        fstride = FRAME_HDR;
+        std::vector<int32_t> f0;
+        for (const auto &r : roots) f0.insert(f0.end(), r.begin(), r.end());
+        F = F0;
+        CK(upload(W.front[0], f0, st), "upload roots");
+        while (F > 0 && depth < max_levels) {
+            if (o.split_depth <= 0 && F >= target_frames) break;
+            CK(W.counts.ensure((size_t)F * 4), "alloc counts");
+            CK(W.offs.ensure((size_t)F * 8), "alloc offsets");
+            CK(W.scan_tmp.ensure(scan_tmp_bytes(F)), "alloc scan");
+            CK(W.total.ensure(16), "alloc total");
+            CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(),
+                            nullptr, nullptr, 0, count_ctr, directed ? 1 : 0, st), "split count");
+            launches += 4;   // split count + three scan kernels
+            CK(launch_scan(W.counts.as<int32_t>(), W.offs.as<long long>(), F, W.total.as<long long>(),
+                           W.scan_tmp.p, W.scan_tmp.cap, st), "split scan");
+            long long total = 0;
+            CK(cudaMemcpyAsync(&total, W.total.p, 8, cudaMemcpyDeviceToHost, st), "read split total");
+            CK(cudaStreamSynchronize(st), "split sync");
+            const long long need = total * (FRAME_HDR + depth + 1);
+            if (need > FRONTIER_MAX_INTS) break;   // keep the current frontier
+            CK(W.front[cur ^ 1].ensure((size_t)std::max<long long>(need, 1) * 4), "alloc frontier");
+            CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(),
+                            W.offs.as<long long>(), W.front[cur ^ 1].as<int32_t>(), 1, count_ctr, directed ? 1 : 0,
+                            st), "split write");
+            ++launches;
+            cur ^= 1;
+            F = total;
+            ++depth;
+            if (trace_on())
+                std::fprintf(stderr, "[sge] split depth %d frames %lld at %.3f ms\n", depth, F, now_ms() - t_start);
+        }
+        fstride = FRAME_HDR + depth;
     }
 
     // ------------------------------------------------- persistent search
@@ -748,7 +814,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         std::memset(&C, 0, sizeof(C));
         C.front = W.front[cur].as<int32_t>();
         C.nfront = nfront;
-        C.fstride = FRAME_HDR + depth;
+        C.fstride = fstride;
         C.shard_index = shard_index;
         C.shard_count = shard_count;
         C.pcap = POOL_CELLS;
@@ -769,6 +835,11 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         C.budget = o.state_budget;
         C.donate = o.no_donation ? 0 : 1;
         C.gran = o.steal_granularity > 0 ? o.steal_granularity : 2;
+        // donation cadence: the CSR kernel's deep, narrow searches need it often; the
+        // bitset kernel's short expansions lose more to donation churn than they gain
+        const bool bits_k = kernel == SGE_KERNEL_BITSET;
+        C.donate_iters = o.donate_every_iters > 0 ? o.donate_every_iters : (bits_k ? (1 << 30) : 1024);
+        C.donate_ns = (unsigned long long)(o.donate_every_us > 0 ? o.donate_every_us : (bits_k ? 2000 : 500)) * 1000ull;
         if (!W.ev0) {
             CK(cudaEventCreate(&W.ev0), "event");
             CK(cudaEventCreate(&W.ev1), "event");
@@ -969,6 +1040,25 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
                 bits[(size_t)v * T->dw + (w >> 6)] |= 1ull << (w & 63);
             }
         CK(upload(T->adj, bits, st), "upload adjacency bitset");
+    } else if (n > BITSET_MAX_N) {
+        // hub rows: the highest-degree vertices get a bitset row (rule 4 becomes one bit test)
+        std::vector<int32_t> order;
+        for (int v = 0; v < n; ++v)
+            if (g.odeg[v] >= HUB_MIN_DEGREE) order.push_back(v);
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            return g.odeg[a] != g.odeg[b] ? g.odeg[a] > g.odeg[b] : a < b;
+        });
+        const long long max_hubs = HUB_BYTES / ((long long)T->dw * 8);
+        if ((long long)order.size() > max_hubs) order.resize((size_t)max_hubs);
+        if (!order.empty()) {
+            std::vector<int32_t> slot((size_t)n, -1);
+            for (size_t i = 0; i < order.size(); ++i) slot[order[i]] = (int32_t)i;
+            CK(upload(T->hub_slot, slot, st), "upload hub slots");
+            CK(upload(T->hub_list, order, st), "upload hub list");
+            CK(T->hub_bits.ensure(order.size() * (size_t)T->dw * 8), "alloc hub rows");
+            CK(launch_build_hubs(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), T->hub_list.as<int32_t>(),
+                                 (int)order.size(), T->dw, T->hub_bits.as<uint64_t>(), st), "hub rows");
+        }
     }
     CK(cudaStreamSynchronize(st), "target upload");
     std::lock_guard<std::mutex> gd(ctx->mu);
@@ -1219,6 +1309,8 @@ sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
     C.deadline_ns = time_limit_ms > 0 ? (unsigned long long)time_limit_ms * 1000000ull : 0ull;
     C.donate = 1;
     C.gran = 2;
+    C.donate_iters = 1024;
+    C.donate_ns = 500000ull;
     int grid = 0;
     ok(launch_search(1, djob, C, k, 1, 0, 0, 0, &grid, st));
     unsigned long long hc[4] = {0, 0, 0, 0};
@@ -1249,7 +1341,7 @@ const char *sge_last_error(sge_ctx *ctx) {
 namespace {
 
 constexpr int SERVE_SLOTS = 4;               // concurrent launch groups (one stream each)
-constexpr int SERVE_GROUP_MAX = 64;          // queries admitted into one launch
+constexpr int SERVE_GROUP_MAX = 512;         // queries admitted into one launch
 constexpr long long SERVE_BYTES = 2ll << 30; // device memory budget for admitted queries
 
 long long query_bytes(const TargetRec &t, const PatternRec &p) {
@@ -1285,12 +1377,7 @@ void serve_worker(sge_ctx *ctx) {
         std::vector<PairReq> reqs;
         for (auto &r : group) reqs.push_back({r->tid, r->pid});
         std::vector<sge_result> res(group.size());
-        sge_opts o = group[0]->opts;
-        if (o.blocks_per_sm <= 0) {
-            // half of the resident blocks per group, so concurrent groups overlap on the device
-            int occ = 0;
-            if (search_blocks_per_sm(1, KMAX, 1, 0, &occ) == cudaSuccess && occ > 1) o.blocks_per_sm = occ / 2;
-        }
+        const sge_opts o = group[0]->opts;
         sge_status rc = run_pairs(ctx, W, st, reqs, &o, res.data(), false, nullptr, 0);
         const double t_done = now_ms();
         {

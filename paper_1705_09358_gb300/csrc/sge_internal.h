@@ -69,6 +69,8 @@ struct TargetView {
     const int2 *vld;            // {label, out-degree}
     const int32_t *indeg;       // directed
     const uint64_t *adj;        // adjacency bitset rows (undirected, small n) or null
+    const int32_t *hub_slot;    // large undirected targets: bitset row of vertex v, or -1
+    const uint64_t *hub_bits;   // hub rows, dw words each
 };
 
 struct PatternView {
@@ -121,6 +123,8 @@ struct SearchCtl {
     long long budget;           // states budget per job, 0 = none
     int32_t donate;             // work donation on/off
     int32_t gran;               // most frames per donation
+    int32_t donate_iters;       // a warp donates at most once per this many iterations ...
+    unsigned long long donate_ns; // ... or per this much device time, whichever comes first
     uint64_t *slab;             // bitset kernel: per-warp level bitsets (search_slab_bytes)
 };
 
@@ -142,6 +146,13 @@ cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const 
 cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, int depth,
                          int32_t *counts, const long long *offs, int32_t *fout, int pass,
                          int count_ctr, int directed, cudaStream_t st);
+// The whole split as one cooperative launch (see k_split_coop); result[4] =
+// {final frame count, final buffer 0/1, levels done, last level's child count};
+// wtot needs one entry per warp of the grid (at most wtot_cap).
+cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, int stride,
+                              long long cap, long long target, int max_levels, long long *wtot, long long wtot_cap,
+                              unsigned *bar, long long *result, int *status, int count_ctr, int directed,
+                              cudaStream_t st);
 cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,
                         void *tmp, size_t tmp_bytes, cudaStream_t st);
 size_t scan_tmp_bytes(long long n);
@@ -156,6 +167,10 @@ cudaError_t launch_pool_init(unsigned long long *seq, int cap, cudaStream_t st);
 size_t search_smem_bytes(int kernel, int kmax, int nwl);
 // Global scratch the search kernel needs for a grid of `grid` blocks.
 size_t search_slab_bytes(int kernel, int kmax, int nwl, long long grid);
+
+// Adjacency bitset rows of the hub vertices `hubs[0..h)` (rows zeroed first).
+cudaError_t launch_build_hubs(const int32_t *rowptr, const int32_t *col, const int32_t *hubs, int h, int dw,
+                              uint64_t *bits, cudaStream_t st);
 
 // Fixed scratch of sge_count_noalloc (sge_noalloc.cu): the current device's
 // address of the library's static device array, set up once per device.

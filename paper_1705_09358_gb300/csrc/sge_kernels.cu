@@ -31,8 +31,8 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int BLOCK = WARPS_PER_BLOCK * 32;
-constexpr int CHECK_EVERY = 64;          // iterations between donation / abort checks
-constexpr int DONATE_BACKOFF = 1024;     // iterations without donating after a donation
+constexpr unsigned long long CHECK_NS = 20000;         // device time between donation / abort checks
+constexpr unsigned long long CANCEL_CHECK_NS = 1000000; // device time between reads of the host cancel word
 constexpr int DONATE_MIN_LEVELS = 2;     // a donated node keeps at least this many levels below it
 constexpr long long IDLE_SPIN_LIMIT = 1ll << 31;
 constexpr int QUEUE_ATTEMPTS = 64;
@@ -139,6 +139,9 @@ __device__ __forceinline__ bool feasible(const JobDesc &J, const PosInfo &P, int
         if (!DIR) {
             if (J.t.adj != nullptr && !chk) {
                 const uint64_t w = __ldg(J.t.adj + (size_t)x * J.t.dw + (c >> 6));
+                if (!((w >> (c & 63)) & 1ull)) return false;
+            } else if (J.t.hub_slot != nullptr && !chk && __ldg(J.t.hub_slot + x) >= 0) {
+                const uint64_t w = __ldg(J.t.hub_bits + (size_t)__ldg(J.t.hub_slot + x) * J.t.dw + (c >> 6));
                 if (!((w >> (c & 63)) & 1ull)) return false;
             } else if (!row_has(J.t.rowptr, J.t.col, J.t.elab, x, c, be.lab_out, chk)) {
                 return false;
@@ -394,6 +397,10 @@ __global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int3
         const bool leaf = depth + 1 == k;
         const PosInfo P = J.pos[depth];
         const Src S = cand_source(J, P, M);
+        // a range frame scans candidates [beg, end); the node's states are counted by its first range
+        const int rbeg = fr[2], rend = fr[3];
+        const int c_lo = rbeg >= 0 ? rbeg : 0, c_hi = rbeg >= 0 ? min(rend, S.len) : S.len;
+        const bool count_states = rbeg <= 0;
         unsigned long long psum = 0;
         if (pass == 1 && leaf) {
             for (int t = lane; t < depth; t += 32) psum += gterm(J.pos[t].pv, M[t]);
@@ -402,11 +409,11 @@ __global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int3
         const long long obase = (pass == 1 && !leaf) ? offs[f] : 0;
         long long child = 0;
         unsigned long long nodes = 0, hs = 0;
-        for (int c0 = 0; c0 < S.len; c0 += 32) {
+        for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
             const int idx = c0 + lane;
             bool ok = false;
             int c = -1;
-            if (idx < S.len) {
+            if (idx < c_hi) {
                 c = S.ptr ? __ldg(S.ptr + S.base + idx) : idx;
                 ok = feasible<DIR>(J, P, depth, c, (S.ptr && P.par >= 0) ? S.base + idx : -1, M);
             }
@@ -434,7 +441,7 @@ __global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int3
         } else if (count_ctr) {
             hs = warp_sum(hs);
             if (lane == 0) {
-                atomicAdd(J.ctr + 1, (unsigned long long)S.len);
+                if (count_states) atomicAdd(J.ctr + 1, (unsigned long long)S.len);
                 atomicAdd(J.ctr + 2, nodes);
                 if (leaf) {
                     atomicAdd(J.ctr + 0, nodes);
@@ -443,6 +450,175 @@ __global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int3
             }
         }
         __syncwarp();
+    }
+}
+
+// ========================================================= device split
+//
+// The breadth-first split as one cooperative launch: every level is a count
+// pass and a write pass over the current frontier, separated by a grid
+// barrier; children are appended atomically (their order is irrelevant
+// outside sharded runs).  The loop stops when the frontier reaches `target`
+// frames, is empty, would overflow `cap`, or `max_levels` levels are done.
+// Frames have a fixed stride (FRAME_HDR + kmax).
+
+__device__ __forceinline__ long long block_excl_scan(long long x, long long *total);
+
+constexpr unsigned long long BARRIER_GUARD_NS = 60ull * 1000000000ull;   // hang guard of one barrier
+
+// Grid barrier for a cooperative launch (all blocks co-resident).  The wait
+// is bounded: after BARRIER_GUARD_NS the block records an error and goes on.
+__device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, int *status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer();
+            unsigned backoff = 32;
+            while (*vgen == g) {
+                __nanosleep(backoff);
+                if (backoff < 1024) backoff <<= 1;
+                if (globaltimer() - t0 > BARRIER_GUARD_NS) { set_status(status, -3); break; }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+struct SplitCtl {
+    int32_t *buf0, *buf1;       // frame buffers, `stride` ints per frame, `cap` frames each
+    int stride;
+    long long cap;
+    long long target;           // stop once the frontier has this many frames
+    int max_levels;
+    long long *wtot;            // [warps]: children per warp, then the warps' exclusive offsets
+    unsigned *bar;              // [2]: barrier count, generation (zeroed by the host)
+    long long *result;          // [4]: final frame count, final buffer (0/1), levels done, last total
+    int *status;
+    int count_ctr;              // 0 in shards other than 0: levels above the frontier are counted once
+};
+
+// One frame of a split level: count its children (pass 0) or write them from
+// `out` on in candidate order and add its counters (pass 1).  Returns the
+// number of children.
+template <bool DIR>
+__device__ __forceinline__ long long split_frame(const JobDesc *jobs, const int32_t *fr, int *M, int pass,
+                                                 int32_t *fout, long long out, int stride, int count_ctr) {
+    const int lane = threadIdx.x & 31;
+    const int j = fr[0], depth = fr[1], rbeg = fr[2], rend = fr[3];
+    const JobDesc &J = jobs[j];
+    for (int t = lane; t < depth; t += 32) M[t] = fr[FRAME_HDR + t];
+    __syncwarp();
+    const bool leaf = depth + 1 == J.k;
+    const PosInfo P = J.pos[depth];
+    const Src src = cand_source(J, P, M);
+    const int c_lo = rbeg >= 0 ? rbeg : 0, c_hi = rbeg >= 0 ? min(rend, src.len) : src.len;
+    unsigned long long psum = 0, nodes = 0, hs = 0;
+    long long child = 0;
+    if (pass == 1 && leaf && count_ctr) {
+        for (int t = lane; t < depth; t += 32) psum += gterm(J.pos[t].pv, M[t]);
+        psum = warp_sum(psum);
+    }
+    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+        const int idx = c0 + lane;
+        bool ok = false;
+        int c = -1;
+        if (idx < c_hi) {
+            c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
+            ok = feasible<DIR>(J, P, depth, c, (src.ptr && P.par >= 0) ? src.base + idx : -1, M);
+        }
+        const unsigned bal = __ballot_sync(FULL, ok);
+        const int cnt = __popc(bal);
+        if (pass == 1) {
+            nodes += cnt;
+            if (leaf) {
+                if (ok && count_ctr) {
+                    hs += fmix64(psum + gterm(P.pv, c));
+                    if (J.mbuf) emit_match(J, M, depth, c);
+                }
+            } else if (ok) {
+                int32_t *dst = fout + (out + child + __popc(bal & ((1u << lane) - 1u))) * stride;
+                dst[0] = j; dst[1] = depth + 1; dst[2] = -1; dst[3] = -1;
+                for (int t = 0; t < depth; ++t) dst[FRAME_HDR + t] = M[t];
+                dst[FRAME_HDR + depth] = c;
+            }
+        }
+        if (!leaf) child += cnt;
+    }
+    if (pass == 1 && count_ctr) {
+        hs = warp_sum(hs);
+        if (lane == 0) {
+            if (rbeg <= 0) atomicAdd(J.ctr + 1, (unsigned long long)src.len);
+            atomicAdd(J.ctr + 2, nodes);
+            if (leaf) {
+                atomicAdd(J.ctr + 0, nodes);
+                atomicAdd(J.ctr + 3, hs);
+            }
+        }
+    }
+    __syncwarp();
+    return child;
+}
+
+template <bool DIR>
+__global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long long f0, SplitCtl S) {
+    __shared__ int Msh[WARPS_PER_BLOCK][KMAX];
+    __shared__ long long carry;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *M = Msh[wib];
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long F = f0, total = 0;
+    int cur = 0, level = 0;
+    for (; level < S.max_levels; ++level) {
+        if (F == 0 || F >= S.target) break;
+        const int32_t *fin = cur ? S.buf1 : S.buf0;
+        int32_t *fout = cur ? S.buf0 : S.buf1;
+        // each warp owns a contiguous slice of the frontier, so children come out in search order
+        const long long lo = F * w / nw, hi = F * (w + 1) / nw;
+        long long mine = 0;
+        for (long long f = lo; f < hi; ++f)
+            mine += split_frame<DIR>(jobs, fin + f * S.stride, M, 0, fout, 0, S.stride, S.count_ctr);
+        if (lane == 0) S.wtot[w] = mine;
+        grid_barrier(S.bar, S.bar + 1, S.status);
+        if (blockIdx.x == 0) {
+            // exclusive scan of the per-warp counts (one block, chunk by chunk)
+            if (threadIdx.x == 0) carry = 0;
+            __syncthreads();
+            for (long long b = 0; b < nw; b += BLOCK) {
+                const long long i = b + threadIdx.x;
+                const long long x = i < nw ? S.wtot[i] : 0;
+                long long tot;
+                const long long ex = block_excl_scan(x, &tot);
+                if (i < nw) S.wtot[i] = carry + ex;
+                __syncthreads();
+                if (threadIdx.x == 0) carry += tot;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) S.result[3] = carry;
+        }
+        grid_barrier(S.bar, S.bar + 1, S.status);
+        total = *(volatile long long *)(S.result + 3);
+        if (total > S.cap) break;      // keep the current frontier (uniform decision)
+        const long long out = *(volatile long long *)(S.wtot + w);
+        long long written = 0;
+        for (long long f = lo; f < hi; ++f)
+            written += split_frame<DIR>(jobs, fin + f * S.stride, M, 1, fout, out + written, S.stride, S.count_ctr);
+        grid_barrier(S.bar, S.bar + 1, S.status);
+        F = total;
+        cur ^= 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.result[0] = F;
+        S.result[1] = cur;
+        S.result[2] = level;
     }
 }
 
@@ -650,17 +826,30 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
 // Periodic checks by lane 0: cancellation, deadline, budget, other warps'
 // errors.  Returns nonzero (warp-uniform) when the warp must stop.
 __device__ __forceinline__ int must_stop(const SearchCtl &C, const JobDesc &J, unsigned long long local_states,
-                                         unsigned long long deadline) {
+                                         unsigned long long deadline, unsigned long long now,
+                                         unsigned long long &last_cancel) {
     int stop = 0;
     if ((threadIdx.x & 31) == 0) {
+        const bool read_cancel = C.cancel != nullptr && now - last_cancel >= CANCEL_CHECK_NS;
+        if (read_cancel) last_cancel = now;
         if (load_relaxed(C.status) != 0) stop = 1;
-        else if (C.cancel != nullptr && *C.cancel != 0) { set_status(C.status, -6); stop = 1; }
+        else if (read_cancel && *C.cancel != 0) { set_status(C.status, -6); stop = 1; }
         else if (deadline != 0 && globaltimer() > deadline) { set_status(C.status, -5); stop = 1; }
         else if (C.budget > 0 && (long long)(*(volatile unsigned long long *)(J.ctr + 1) + local_states) > C.budget) {
             set_status(C.status, -4); stop = 1;
         }
     }
     return __shfl_sync(FULL, stop, 0);
+}
+
+// Warp-uniform: has CHECK_NS of device time passed since the last check?
+__device__ __forceinline__ bool time_to_check(unsigned long long &last) {
+    unsigned long long now = 0;
+    if ((threadIdx.x & 31) == 0) now = globaltimer();
+    now = __shfl_sync(FULL, now, 0);
+    if (now - last < CHECK_NS) return false;
+    last = now;
+    return true;
 }
 
 __device__ __forceinline__ bool donation_wanted(const SearchCtl &C) {
@@ -703,9 +892,9 @@ __host__ __device__ __forceinline__ size_t csr_smem_per_warp(int kmax) {
 }
 
 struct CsrJob {
-    const int32_t *rowptr, *col, *elab, *irowptr, *icol, *ielab, *indeg, *ulist;
+    const int32_t *rowptr, *col, *elab, *irowptr, *icol, *ielab, *indeg, *ulist, *hub_slot;
     const int2 *vld;
-    const uint64_t *filt, *adj;
+    const uint64_t *filt, *adj, *hub_bits;
     const BackEdge *back;
     int n, dw, k, flags;
 };
@@ -740,6 +929,9 @@ __device__ __forceinline__ bool csr_feasible(const CsrJob &B, const PosC &p, int
             if (B.adj != nullptr && !chk) {
                 const uint64_t w = __ldg(B.adj + (size_t)x * B.dw + (c >> 6));
                 if (!((w >> (c & 63)) & 1ull)) return false;
+            } else if (B.hub_slot != nullptr && !chk && __ldg(B.hub_slot + x) >= 0) {
+                const uint64_t w = __ldg(B.hub_bits + (size_t)__ldg(B.hub_slot + x) * B.dw + (c >> 6));
+                if (!((w >> (c & 63)) & 1ull)) return false;
             } else if (!row_has(B.rowptr, B.col, B.elab, x, c, be.lab_out, chk)) {
                 return false;
             }
@@ -764,7 +956,8 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
-    long long iter = 0, quiet_until = 0;
+    long long iter = 0, last_don_iter = 0;
+    unsigned long long last_check = 0, last_don_ns = 0, last_cancel = 0;
     int cur_job = -1;
     CsrJob B;
     while (acquire_frame(C, M, fr, deadline)) {
@@ -774,6 +967,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             B.rowptr = J.t.rowptr; B.col = J.t.col; B.elab = J.t.elab;
             B.irowptr = J.t.irowptr; B.icol = J.t.icol; B.ielab = J.t.ielab; B.indeg = J.t.indeg;
             B.ulist = J.ulist; B.vld = J.t.vld; B.filt = J.filt; B.adj = J.t.adj; B.back = J.back;
+            B.hub_slot = J.t.hub_slot; B.hub_bits = J.t.hub_bits;
             B.n = J.t.n; B.dw = J.t.dw; B.k = J.k; B.flags = J.flags;
             for (int t = lane; t < B.k; t += 32) {
                 const PosInfo P = J.pos[t];
@@ -812,21 +1006,23 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
         };
         {
             const int len = setup(d0, fr.beg, fr.end);
-            if (fr.beg < 0) st += (unsigned long long)len;
+            if (fr.beg <= 0) st += (unsigned long long)len;   // a node's first (or only) range counts its states
         }
         int lvl = d0;
         bool stopped = false;
         for (;;) {
-            if (((++iter) & (CHECK_EVERY - 1)) == 0) {
+            if (((++iter) & 7) == 0 && time_to_check(last_check)) {
                 if (C.budget > 0) {
                     if (lane == 0) atomicAdd(J.ctr + 1, st);
                     st = 0;
                 }
-                if (must_stop(C, J, st, deadline)) { stopped = true; break; }
-                if (iter >= quiet_until && donation_wanted(C)) {
+                if (must_stop(C, J, st, deadline, last_check, last_cancel)) { stopped = true; break; }
+                if ((iter - last_don_iter >= C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
+                    donation_wanted(C)) {
                     // donate the shallowest unexplored work: half of an unscanned
                     // range, else up to `gran` pending survivors as new search nodes
-                    quiet_until = iter + DONATE_BACKOFF;
+                    last_don_iter = iter;
+                    last_don_ns = last_check;
                     for (int l = d0; l <= lvl && l + 1 + DONATE_MIN_LEVELS <= k; ++l) {
                         LvCsr &L = lv[l];
                         const int rem = L.end - L.cur;
@@ -982,7 +1178,8 @@ __device__ __forceinline__ void used_flip(uint64_t *used, int v) {
 // and either hash them as matches (leaf) or keep them as pending survivors.
 template <int NWL>
 __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W, int i, bool leaf,
-                                           unsigned long long &st, unsigned long long &hs, unsigned long long &ab) {
+                                           unsigned long long &st, unsigned long long &hs, unsigned long long &ab,
+                                           int vlo = 0, int vhi = 0x7fffffff, bool count_len = true) {
     const int lane = threadIdx.x & 31;
     const PosB p = W.tab[i];
     const int dw = B.dw;
@@ -1014,12 +1211,22 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
             if (q < dw) s[w] &= __ldg(X + q);
         }
     }
-    st += (unsigned long long)len;
+    if (count_len) st += (unsigned long long)len;
     ab += (unsigned long long)((p.par >= 0 ? 2 : 1) + p.bc) * (unsigned long long)dw * 8ull;
     int cnt = 0;
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
         s[w] &= ~W.used[w * 32 + lane];
+        if (vlo > 0 || vhi != 0x7fffffff) {
+            // a range frame: keep the candidates with vertex ids in [vlo, vhi]
+            const int b0 = (lane + 32 * w) * 64;
+            if (vhi < b0 || vlo > b0 + 63) {
+                s[w] = 0;
+            } else {
+                const int lo = vlo > b0 ? vlo - b0 : 0, hi = vhi < b0 + 63 ? vhi - b0 : 63;
+                s[w] &= (~0ull << lo) & (~0ull >> (63 - hi));
+            }
+        }
         cnt += __popcll(s[w]);
     }
     const int total = __reduce_add_sync(FULL, (unsigned)cnt);
@@ -1144,7 +1351,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
 
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
-    long long iter = 0, quiet_until = 0;
+    long long iter = 0, last_don_iter = 0;
+    unsigned long long last_check = 0, last_don_ns = 0, last_cancel = 0;
     int cur_job = -1;
     BitsJob B;
     while (acquire_frame(C, M, fr, deadline)) {
@@ -1176,22 +1384,49 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             __syncwarp();
         }
         bool stopped = false;
+        // a range frame covers candidates [beg, end) of its node: as the candidate
+        // lists are ascending, that is the vertex-id interval [first, last]
+        int vlo = 0, vhi = 0x7fffffff;
+        if (fr.beg >= 0) {
+            const PosB p = W.tab[d0];
+            const int32_t *lst = nullptr;
+            int b0 = 0, len = 0;
+            if (p.par >= 0) {
+                const int a = M[p.par];
+                lst = J.t.col;
+                b0 = __ldg(J.t.rowptr + a);
+                len = __ldg(J.t.rowptr + a + 1) - b0;
+            } else if (J.flags & JOB_RIDS) {
+                lst = J.ulist;
+                b0 = J.pos[d0].uoff;
+                len = J.pos[d0].ucnt;
+            } else {
+                len = J.t.n;
+            }
+            const int e = min(fr.end, len);
+            if (fr.beg >= e) { vlo = 1; vhi = 0; }
+            else if (lst) { vlo = __ldg(lst + b0 + fr.beg); vhi = __ldg(lst + b0 + e - 1); }
+            else { vlo = fr.beg; vhi = e - 1; }
+        }
+        const bool count_len = fr.beg <= 0;
         if (d0 == k - 1) {
-            const int c = bits_expand<NWL>(B, J, W, d0, true, st, hs, ab);
+            const int c = bits_expand<NWL>(B, J, W, d0, true, st, hs, ab, vlo, vhi, count_len);
             nd += c; mt += c;
         } else {
-            nd += bits_expand<NWL>(B, J, W, d0, false, st, hs, ab);
+            nd += bits_expand<NWL>(B, J, W, d0, false, st, hs, ab, vlo, vhi, count_len);
             int lvl = d0;
             for (;;) {
-                if (((++iter) & (CHECK_EVERY - 1)) == 0) {
+                if (((++iter) & 7) == 0 && time_to_check(last_check)) {
                     if (C.budget > 0) {
                         if (lane == 0) atomicAdd(J.ctr + 1, st);
                         st = 0;
                     }
-                    if (must_stop(C, J, st, deadline)) { stopped = true; break; }
-                    if (iter >= quiet_until && donation_wanted(C)) {
+                    if (must_stop(C, J, st, deadline, last_check, last_cancel)) { stopped = true; break; }
+                    if ((iter - last_don_iter >= C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
+                        donation_wanted(C)) {
                         // donate up to `gran` pending survivors of the shallowest level that has some
-                        quiet_until = iter + DONATE_BACKOFF;
+                        last_don_iter = iter;
+                        last_don_ns = last_check;
                         for (int l = d0; l <= lvl && l + 1 + DONATE_MIN_LEVELS <= k; ++l) {
                             int given = 0;
                             while (given < C.gran) {
@@ -1303,6 +1538,30 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, int stride,
+                              long long cap, long long target, int max_levels, long long *wtot, long long wtot_cap,
+                              unsigned *bar, long long *result, int *status, int count_ctr, int directed,
+                              cudaStream_t st) {
+    SplitCtl S;
+    S.buf0 = buf0; S.buf1 = buf1; S.stride = stride; S.cap = cap; S.target = target; S.max_levels = max_levels;
+    S.wtot = wtot; S.bar = bar; S.result = result; S.status = status; S.count_ctr = count_ctr;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    void *fn = directed ? (void *)k_split_coop<true> : (void *)k_split_coop<false>;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BLOCK, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    if ((long long)sms * occ * WARPS_PER_BLOCK > wtot_cap) occ = (int)(wtot_cap / ((long long)sms * WARPS_PER_BLOCK));
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    // all blocks must be co-resident for the grid barrier: a cooperative launch guarantees it
+    dim3 grid(sms * occ), block(BLOCK);
+    void *args[] = {(void *)&jobs, (void *)&f0, (void *)&S};
+    return cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st);
+}
+
 size_t scan_tmp_bytes(long long n) {
     const long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     return (size_t)(tiles + 1) * sizeof(long long);
@@ -1323,6 +1582,27 @@ cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long lon
 }
 
 int search_warps_per_block() { return WARPS_PER_BLOCK; }
+
+namespace {
+// One block per hub: set the bit of every neighbour in the hub's row.
+__global__ void k_build_hubs(const int32_t *rowptr, const int32_t *col, const int32_t *hubs, int dw, uint64_t *bits) {
+    const int x = hubs[blockIdx.x];
+    uint64_t *row = bits + (size_t)blockIdx.x * dw;
+    for (int e = rowptr[x] + threadIdx.x; e < rowptr[x + 1]; e += blockDim.x) {
+        const int y = col[e];
+        atomicOr((unsigned long long *)(row + (y >> 6)), 1ull << (y & 63));
+    }
+}
+}  // namespace
+
+cudaError_t launch_build_hubs(const int32_t *rowptr, const int32_t *col, const int32_t *hubs, int h, int dw,
+                              uint64_t *bits, cudaStream_t st) {
+    if (h <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)h * dw * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    k_build_hubs<<<h, BLOCK, 0, st>>>(rowptr, col, hubs, dw, bits);
+    return cudaGetLastError();
+}
 
 namespace {
 __global__ void k_pool_init(unsigned long long *seq, int cap) {
