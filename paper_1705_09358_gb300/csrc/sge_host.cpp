@@ -471,7 +471,7 @@ int pow2_at_least(int x) {
 // launch sequence on `st` with workspace `W`.
 sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
                      const std::vector<int> &idx, const sge_opts &o, sge_result *out, bool enumerate,
-                     std::vector<int32_t> *match_rows, long long match_cap) {
+                     std::vector<int32_t> *match_rows, long long match_cap, bool serving) {
     const double t_start = now_ms();
     long long launches = 0;   // kernels launched by this call
     const int algo = o.algo;
@@ -740,7 +740,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         int *sstat = reinterpret_cast<int *>(res + 4);
         const cudaError_t le = launch_split_coop(W.jobs.as<JobDesc>(), F0, W.front[0].as<int32_t>(),
                                                  W.front[1].as<int32_t>(), fstride, cap, target, max_levels, wtot,
-                                                 wcap, bar, res, sstat, count_ctr, directed ? 1 : 0, st);
+                                                 wcap, bar, res, sstat, count_ctr, directed ? 1 : 0,
+                                                 serving ? 1 : 0, st);
         if (le == cudaSuccess) {
             ++launches;
             long long r4[4] = {0, 0, 0, 0};
@@ -840,6 +841,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         const bool bits_k = kernel == SGE_KERNEL_BITSET;
         C.donate_iters = o.donate_every_iters > 0 ? o.donate_every_iters : (bits_k ? (1 << 30) : 1024);
         C.donate_ns = (unsigned long long)(o.donate_every_us > 0 ? o.donate_every_us : (bits_k ? 2000 : 500)) * 1000ull;
+        // serving groups: idle warps leave after 20 us so a group's tail frees block slots
+        // for the next group's kernels
+        C.idle_exit_ns = serving ? 20000ull : 0ull;
         if (!W.ev0) {
             CK(cudaEventCreate(&W.ev0), "event");
             CK(cudaEventCreate(&W.ev1), "event");
@@ -908,7 +912,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
 
 sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
                      const sge_opts *opts, sge_result *out, bool enumerate, std::vector<int32_t> *rows,
-                     long long cap) {
+                     long long cap, bool serving = false) {
     sge_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
@@ -939,8 +943,8 @@ sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         }
     }
     sge_status rc = SGE_OK;
-    if (!und.empty()) rc = run_group(ctx, W, st, reqs, und, o, out, enumerate, rows, cap);
-    if (rc == SGE_OK && !dir.empty()) rc = run_group(ctx, W, st, reqs, dir, o, out, enumerate, rows, cap);
+    if (!und.empty()) rc = run_group(ctx, W, st, reqs, und, o, out, enumerate, rows, cap, serving);
+    if (rc == SGE_OK && !dir.empty()) rc = run_group(ctx, W, st, reqs, dir, o, out, enumerate, rows, cap, serving);
     return rc;
 }
 
@@ -1378,7 +1382,8 @@ void serve_worker(sge_ctx *ctx) {
         for (auto &r : group) reqs.push_back({r->tid, r->pid});
         std::vector<sge_result> res(group.size());
         const sge_opts o = group[0]->opts;
-        sge_status rc = run_pairs(ctx, W, st, reqs, &o, res.data(), false, nullptr, 0);
+        // a serving group: idle warps exit early and the split runs one block per SM
+        sge_status rc = run_pairs(ctx, W, st, reqs, &o, res.data(), false, nullptr, 0, true);
         const double t_done = now_ms();
         {
             std::lock_guard<std::mutex> lk(ctx->smu);

@@ -125,6 +125,7 @@ struct SearchCtl {
     int32_t gran;               // most frames per donation
     int32_t donate_iters;       // a warp donates at most once per this many iterations ...
     unsigned long long donate_ns; // ... or per this much device time, whichever comes first
+    unsigned long long idle_exit_ns; // a warp idle this long exits (0 = wait for the end)
     uint64_t *slab;             // bitset kernel: per-warp level bitsets (search_slab_bytes)
 };
 
@@ -152,7 +153,7 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, int stride,
                               long long cap, long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
-                              cudaStream_t st);
+                              int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,
                         void *tmp, size_t tmp_bytes, cudaStream_t st);
 size_t scan_tmp_bytes(long long n);

@@ -768,6 +768,7 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
     bool idle = false;
     long long spins = 0;
     unsigned backoff = 64;
+    unsigned long long idle_since = 0;
     int kind = 0;        // 1 frontier, 2 queue, 0 stop
     long long idx = -1;
     for (;;) {
@@ -787,7 +788,11 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
                 if (kind < 0 && load_relaxed(C.outstanding) == 0) kind = 0;
             }
             if (kind < 0) {
-                if (!idle) { atomicAdd(C.idle, 1); idle = true; }
+                if (!idle) { atomicAdd(C.idle, 1); idle = true; idle_since = globaltimer(); }
+                // optional early exit of a warp that found no work for a while: the warps that
+                // still hold frames finish every queued frame themselves, so no frame is lost,
+                // and the freed block slots serve kernels launched on other streams
+                else if (C.idle_exit_ns != 0 && globaltimer() - idle_since > C.idle_exit_ns) kind = 0;
                 if (++spins > IDLE_SPIN_LIMIT) { set_status(C.status, -5); kind = 0; }
                 else if ((spins & 1023) == 0) {
                     if ((C.cancel != nullptr && *C.cancel != 0)) { set_status(C.status, -6); kind = 0; }
@@ -1176,7 +1181,7 @@ __device__ __forceinline__ void used_flip(uint64_t *used, int v) {
 
 // Expand position i: compute S_i, count its survivors (the accepted nodes),
 // and either hash them as matches (leaf) or keep them as pending survivors.
-template <int NWL>
+template <int NWL, bool RANGE = false>
 __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W, int i, bool leaf,
                                            unsigned long long &st, unsigned long long &hs, unsigned long long &ab,
                                            int vlo = 0, int vhi = 0x7fffffff, bool count_len = true) {
@@ -1217,7 +1222,7 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
         s[w] &= ~W.used[w * 32 + lane];
-        if (vlo > 0 || vhi != 0x7fffffff) {
+        if (RANGE) {
             // a range frame: keep the candidates with vertex ids in [vlo, vhi]
             const int b0 = (lane + 32 * w) * 64;
             if (vhi < b0 || vlo > b0 + 63) {
@@ -1409,11 +1414,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             else { vlo = fr.beg; vhi = e - 1; }
         }
         const bool count_len = fr.beg <= 0;
-        if (d0 == k - 1) {
-            const int c = bits_expand<NWL>(B, J, W, d0, true, st, hs, ab, vlo, vhi, count_len);
-            nd += c; mt += c;
+        const bool leaf0 = d0 == k - 1;
+        const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, d0, leaf0, st, hs, ab, vlo, vhi, count_len)
+                                   : bits_expand<NWL>(B, J, W, d0, leaf0, st, hs, ab);
+        nd += c0;
+        if (leaf0) {
+            mt += c0;
         } else {
-            nd += bits_expand<NWL>(B, J, W, d0, false, st, hs, ab, vlo, vhi, count_len);
             int lvl = d0;
             for (;;) {
                 if (((++iter) & 7) == 0 && time_to_check(last_check)) {
@@ -1541,7 +1548,7 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, int stride,
                               long long cap, long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
-                              cudaStream_t st) {
+                              int blocks_per_sm, cudaStream_t st) {
     SplitCtl S;
     S.buf0 = buf0; S.buf1 = buf1; S.stride = stride; S.cap = cap; S.target = target; S.max_levels = max_levels;
     S.wtot = wtot; S.bar = bar; S.result = result; S.status = status; S.count_ctr = count_ctr;
@@ -1554,6 +1561,7 @@ cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BLOCK, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
     if ((long long)sms * occ * WARPS_PER_BLOCK > wtot_cap) occ = (int)(wtot_cap / ((long long)sms * WARPS_PER_BLOCK));
     if (occ < 1) return cudaErrorInvalidConfiguration;
     // all blocks must be co-resident for the grid barrier: a cooperative launch guarantees it

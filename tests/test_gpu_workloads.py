@@ -129,3 +129,21 @@ def test_cancel_from_another_thread():
     assert not th.is_alive()
     assert out["r"]["rc"] == sge.SGE_ERR_CANCELLED
     assert E.count(tid, E.load_pattern(complete(2)))["matches"] == 48 * 47
+
+
+def test_cl100k_rids_variants_sample():
+    """RI-DS (all three variants) on the 100k-vertex serving target: domains of
+    k x 100,000 bits per query, checked against the live oracle."""
+    import oracle
+    t = workload("cl100k_target")
+    w = workload("cl100k")
+    E = engine()
+    tid = E.load_target(t)
+    pats = w.patterns[:40]
+    pids = [E.load_pattern(p) for p in pats]
+    ot = oracle.Target(t)
+    for algo in (1, 2, 3):
+        rc, rows = E.count_batch([tid] * len(pids), pids, algo=algo)
+        for i, p in enumerate(pats):
+            want = oracle.run(ot, p, algo)
+            assert counters(rows[i]) == counters(want), (algo, i)
