@@ -721,15 +721,18 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     bool split_done = F0 == 0;
     const int max_levels = std::max(0, std::min(o.split_depth > 0 ? o.split_depth : INT_MAX, kmax - 1));
     if (!split_done) {
-        // the whole split as one cooperative launch; frames of stride FRAME_HDR + kmax
-        fstride = FRAME_HDR + kmax;
-        const long long target = o.split_depth > 0 ? LLONG_MAX : target_frames;
-        const long long cap =
-            std::max<long long>(F0, std::min<long long>(FRONTIER_MAX_INTS / fstride, 8 * target_frames + F0));
-        CK(W.front[0].ensure((size_t)cap * fstride * 4), "alloc frontier");
-        CK(W.front[1].ensure((size_t)cap * fstride * 4), "alloc frontier");
-        CK(cudaMemcpy2DAsync(W.front[0].p, (size_t)fstride * 4, roots.data(), sizeof(roots[0]), sizeof(roots[0]),
-                             (size_t)F0, cudaMemcpyHostToDevice, st), "upload roots");
+        // the whole split as one cooperative launch.  Auto depth, CSR kernel: breadth-first
+        // for as long as the next level fits the frontier budget (deep, narrow searches are
+        // far cheaper level by level than depth-first, and the split tests candidates the way
+        // the CSR kernel does).  Bitset kernel: stop at the frame target, since its
+        // word-parallel expansion beats the split's per-candidate tests on dense targets.
+        const long long target = o.split_depth > 0 ? LLONG_MAX
+                                 : kernel == SGE_KERNEL_BITSET ? target_frames : (long long)INT_MAX;
+        const long long cap_ints = std::max<long long>(F0 * FRAME_HDR, FRONTIER_MAX_INTS);
+        CK(W.front[0].ensure((size_t)cap_ints * 4), "alloc frontier");
+        CK(W.front[1].ensure((size_t)cap_ints * 4), "alloc frontier");
+        CK(cudaMemcpyAsync(W.front[0].p, roots.data(), (size_t)F0 * sizeof(roots[0]), cudaMemcpyHostToDevice, st),
+           "upload roots");
         const long long wcap = (long long)ctx->sms * 32 * search_warps_per_block();
         const size_t ctl_words = (size_t)wcap + 16;
         CK(W.splitctl.ensure(ctl_words * 8), "alloc split control");
@@ -739,7 +742,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         long long *res = wtot + wcap + 1;
         int *sstat = reinterpret_cast<int *>(res + 4);
         const cudaError_t le = launch_split_coop(W.jobs.as<JobDesc>(), F0, W.front[0].as<int32_t>(),
-                                                 W.front[1].as<int32_t>(), fstride, cap, target, max_levels, wtot,
+                                                 W.front[1].as<int32_t>(), cap_ints, target, max_levels, wtot,
                                                  wcap, bar, res, sstat, count_ctr, directed ? 1 : 0,
                                                  serving ? 1 : 0, st);
         if (le == cudaSuccess) {
@@ -753,6 +756,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             F = r4[0];
             cur = (int)r4[1];
             depth = (int)r4[2];
+            fstride = FRAME_HDR + depth;
             split_done = true;
             if (trace_on())
                 std::fprintf(stderr, "[sge] device split: %d levels, %lld frames at %.3f ms\n", depth, F,

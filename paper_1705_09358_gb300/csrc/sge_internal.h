@@ -147,11 +147,12 @@ cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const 
 cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, int depth,
                          int32_t *counts, const long long *offs, int32_t *fout, int pass,
                          int count_ctr, int directed, cudaStream_t st);
-// The whole split as one cooperative launch (see k_split_coop); result[4] =
+// The whole split as one cooperative launch (see k_split_coop): frames of
+// level L have stride FRAME_HDR + L in buffers of cap_ints ints; result[4] =
 // {final frame count, final buffer 0/1, levels done, last level's child count};
 // wtot needs one entry per warp of the grid (at most wtot_cap).
-cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, int stride,
-                              long long cap, long long target, int max_levels, long long *wtot, long long wtot_cap,
+cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
+                              long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
                               int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,

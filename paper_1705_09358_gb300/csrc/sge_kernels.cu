@@ -493,9 +493,8 @@ __device__ __forceinline__ void grid_barrier(unsigned *count, unsigned *gen, int
 }
 
 struct SplitCtl {
-    int32_t *buf0, *buf1;       // frame buffers, `stride` ints per frame, `cap` frames each
-    int stride;
-    long long cap;
+    int32_t *buf0, *buf1;       // frame buffers of `cap_ints` ints each; a level-L frame has stride FRAME_HDR + L
+    long long cap_ints;
     long long target;           // stop once the frontier has this many frames
     int max_levels;
     long long *wtot;            // [warps]: children per warp, then the warps' exclusive offsets
@@ -581,11 +580,12 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         if (F == 0 || F >= S.target) break;
         const int32_t *fin = cur ? S.buf1 : S.buf0;
         int32_t *fout = cur ? S.buf0 : S.buf1;
+        const int sin = FRAME_HDR + level, sout = FRAME_HDR + level + 1;   // all frames of a level share a depth
         // each warp owns a contiguous slice of the frontier, so children come out in search order
         const long long lo = F * w / nw, hi = F * (w + 1) / nw;
         long long mine = 0;
         for (long long f = lo; f < hi; ++f)
-            mine += split_frame<DIR>(jobs, fin + f * S.stride, M, 0, fout, 0, S.stride, S.count_ctr);
+            mine += split_frame<DIR>(jobs, fin + f * sin, M, 0, fout, 0, sout, S.count_ctr);
         if (lane == 0) S.wtot[w] = mine;
         grid_barrier(S.bar, S.bar + 1, S.status);
         if (blockIdx.x == 0) {
@@ -606,11 +606,11 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         }
         grid_barrier(S.bar, S.bar + 1, S.status);
         total = *(volatile long long *)(S.result + 3);
-        if (total > S.cap) break;      // keep the current frontier (uniform decision)
+        if (total * sout > S.cap_ints) break;   // the next level does not fit: keep this frontier
         const long long out = *(volatile long long *)(S.wtot + w);
         long long written = 0;
         for (long long f = lo; f < hi; ++f)
-            written += split_frame<DIR>(jobs, fin + f * S.stride, M, 1, fout, out + written, S.stride, S.count_ctr);
+            written += split_frame<DIR>(jobs, fin + f * sin, M, 1, fout, out + written, sout, S.count_ctr);
         grid_barrier(S.bar, S.bar + 1, S.status);
         F = total;
         cur ^= 1;
@@ -1545,12 +1545,12 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, int stride,
-                              long long cap, long long target, int max_levels, long long *wtot, long long wtot_cap,
+cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
+                              long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
                               int blocks_per_sm, cudaStream_t st) {
     SplitCtl S;
-    S.buf0 = buf0; S.buf1 = buf1; S.stride = stride; S.cap = cap; S.target = target; S.max_levels = max_levels;
+    S.buf0 = buf0; S.buf1 = buf1; S.cap_ints = cap_ints; S.target = target; S.max_levels = max_levels;
     S.wtot = wtot; S.bar = bar; S.result = result; S.status = status; S.count_ctr = count_ctr;
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
