@@ -32,6 +32,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int BLOCK = WARPS_PER_BLOCK * 32;
 constexpr unsigned long long CHECK_NS = 20000;         // device time between donation / abort checks
+// (the timer is read every 8 iterations of the CSR kernel and every 64 of the bitset kernel,
+// whose iterations are an order of magnitude cheaper)
 constexpr unsigned long long CANCEL_CHECK_NS = 1000000; // device time between reads of the host cancel word
 constexpr int DONATE_MIN_LEVELS = 2;     // a donated node keeps at least this many levels below it
 constexpr long long IDLE_SPIN_LIMIT = 1ll << 31;
@@ -1423,7 +1425,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         } else {
             int lvl = d0;
             for (;;) {
-                if (((++iter) & 7) == 0 && time_to_check(last_check)) {
+                if (((++iter) & 63) == 0 && time_to_check(last_check)) {
                     if (C.budget > 0) {
                         if (lane == 0) atomicAdd(J.ctr + 1, st);
                         st = 0;
