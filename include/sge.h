@@ -71,8 +71,11 @@ typedef struct {
     int32_t split_depth;       /* depth of the breadth-first split; 0 = auto */
     int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 32) */
     int32_t steal_granularity; /* most frames one donation hands out (default 2) */
-    int64_t state_budget;      /* stop after about this many states (0 = none) */
-    int64_t time_limit_ms;     /* stop after about this much search time (0 = none) */
+    int64_t state_budget;      /* stop after about this many states of one pair (0 = none) */
+    int64_t time_limit_ms;     /* stop after about this much search-kernel time (0 = none);
+                                  with either limit set the split stops at the frame
+                                  target, so the search kernel, which checks them, does
+                                  the bulk of the work */
     int32_t kernel;            /* SGE_KERNEL_* */
     int32_t blocks_per_sm;     /* persistent-kernel blocks per SM (0 = occupancy maximum) */
     int32_t shard_index;       /* multi-device form: this device's shard ... */
@@ -170,6 +173,47 @@ sge_status sge_enumerate(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, co
  * SGE_OK or the first error; per-pair errors are in out[i].status. */
 sge_status sge_count_batch(sge_ctx *ctx, int64_t npairs, const int32_t *target_ids,
                            const int32_t *pattern_ids, const sge_opts *opts, sge_result *out);
+
+/* Checkpoint and resume.  The paper's experiments stop a search at a time
+ * limit (Section 5) and lose its work; these calls keep it.
+ *
+ * sge_count_batch_ckpt counts like sge_count_batch.  When the search stops
+ * (state budget, time limit or sge_cancel) it returns BUDGET / TIMEOUT /
+ * CANCELLED, out[i] holds pair i's counters so far, and *ckpt receives a
+ * host blob of *ckpt_bytes bytes, allocated by the library (free it with
+ * sge_free), that records the pairs, the counters and every subtree not yet
+ * searched.  When the search finishes it returns SGE_OK and sets
+ * *ckpt = NULL, *ckpt_bytes = 0.  Other errors as sge_count_batch (no blob).
+ *
+ * sge_resume continues from such a blob (the caller keeps ownership of it;
+ * it may come from another process or context) on a context that has the
+ * same targets and patterns loaded under the same ids.  opts may change the
+ * schedule, budget and time limit; the variant (algo) and shard come from
+ * the blob.  out (npairs entries, see sge_ckpt_info) receives the counters
+ * accumulated over the first call and every resume so far, and *next a new
+ * blob if the search stopped again.  Calling sge_resume until it returns
+ * SGE_OK gives exactly the counters of one uninterrupted sge_count_batch.
+ * Errors: ARG (malformed blob, or ids/sizes that do not match the loaded
+ * graphs), and as sge_count_batch.
+ *
+ * Blob layout (little-endian): header {u64 magic "SGECKPT1", i32 version 1,
+ * i32 algo, i64 npairs, i32 ngroups, i32 0}; npairs x {i32 target id,
+ * i32 pattern id, i32 n_t, i32 k}; npairs x {u64 matches, states, nodes,
+ * hash}; per group (the pairs of one directedness) {i32 kmax, i32 npairs_g,
+ * i64 nframes}, npairs_g x i32 pair index (padded to even), nframes frames
+ * of 4 + kmax i32: [job, depth | 65536 if the range's nodes were already
+ * counted, first, end, image of each of the first depth positions of the
+ * pair's search order], where [first, end) is a range of the candidate list
+ * of position `depth` (first = -1: the whole list). */
+sge_status sge_count_batch_ckpt(sge_ctx *ctx, int64_t npairs, const int32_t *target_ids,
+                                const int32_t *pattern_ids, const sge_opts *opts, sge_result *out,
+                                void **ckpt, int64_t *ckpt_bytes);
+sge_status sge_resume(sge_ctx *ctx, const void *ckpt, int64_t ckpt_bytes, const sge_opts *opts,
+                      sge_result *out, void **next, int64_t *next_bytes);
+/* Pairs and unexplored frames recorded in a blob (ARG if malformed). */
+sge_status sge_ckpt_info(const void *ckpt, int64_t ckpt_bytes, int64_t *npairs, int64_t *nframes);
+/* Free a blob returned by sge_count_batch_ckpt or sge_resume (NULL is fine). */
+void sge_free(void *p);
 
 /* Serving (continuous batching).  sge_serve_submit queues one query and
  * returns at once with a ticket; scheduler threads owned by the context

@@ -31,7 +31,8 @@ ERROR_NAMES = {0: "OK", -1: "ARG", -2: "OOM", -3: "CUDA", -4: "BUDGET", -5: "TIM
 # every entry point declared in include/sge.h
 SYMBOLS = ["sge_create", "sge_destroy", "sge_load_target", "sge_load_pattern", "sge_unload_target",
            "sge_unload_pattern", "sge_count", "sge_enumerate", "sge_count_batch", "sge_serve_submit",
-           "sge_serve_poll", "sge_serve_drain", "sge_cancel", "sge_last_error", "sge_version", "sge_count_noalloc"]
+           "sge_serve_poll", "sge_serve_drain", "sge_cancel", "sge_last_error", "sge_version", "sge_count_noalloc",
+           "sge_count_batch_ckpt", "sge_resume", "sge_ckpt_info", "sge_free"]
 
 
 class sge_opts(C.Structure):
@@ -84,6 +85,12 @@ def load_library(path: str = LIB_PATH):
     lib.sge_serve_poll.argtypes = [P, I64, C.POINTER(I32), C.POINTER(sge_result)]
     lib.sge_serve_drain.argtypes = [P]
     lib.sge_count_noalloc.argtypes = [I32, P, P, P, P, I32, I64, P, P, P, P, P, I64, P]
+    lib.sge_count_batch_ckpt.argtypes = [P, I64, P, P, C.POINTER(sge_opts), P, C.POINTER(C.c_void_p),
+                                         C.POINTER(I64)]
+    lib.sge_resume.argtypes = [P, P, I64, C.POINTER(sge_opts), P, C.POINTER(C.c_void_p), C.POINTER(I64)]
+    lib.sge_ckpt_info.argtypes = [P, I64, C.POINTER(I64), C.POINTER(I64)]
+    lib.sge_free.argtypes = [P]
+    lib.sge_free.restype = None
     lib.sge_cancel.argtypes = [P]
     lib.sge_last_error.argtypes = [P]
     lib.sge_last_error.restype = C.c_char_p
@@ -91,7 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.sge_version.restype = C.c_char_p
     for name in SYMBOLS:
         fn = getattr(lib, name)
-        if fn.restype is C.c_int and name not in ("sge_destroy",):
+        if fn.restype is C.c_int and name not in ("sge_destroy", "sge_free"):
             fn.restype = C.c_int32
     _lib = lib
     return lib
@@ -203,6 +210,61 @@ def sge_count_batch(ctx, tids, pids, opts: sge_opts | None = None, check: bool =
     return int(rc), np.array(arr, copy=True)
 
 
+def _take_blob(ptr: C.c_void_p, nbytes: C.c_int64):
+    """Copy a library-allocated checkpoint blob into bytes and free it (None if there is none)."""
+    if not ptr.value:
+        return None
+    try:
+        return C.string_at(ptr.value, int(nbytes.value))
+    finally:
+        load_library().sge_free(ptr)
+
+
+_STOPS = (-4, -5, -6)   # BUDGET, TIMEOUT, CANCELLED: the search stopped and left a checkpoint
+
+
+def sge_count_batch_ckpt(ctx, tids, pids, opts: sge_opts | None = None, check: bool = True):
+    """As sge_count_batch; returns (rc, rows, checkpoint bytes or None).
+
+    A stop (budget, time limit, cancel) is not an error here: rc says which,
+    rows hold the counters so far and the checkpoint the work left."""
+    tids, pids = _i32(tids), _i32(pids)
+    n = int(tids.shape[0])
+    out = (sge_result * max(n, 1))()
+    ptr, nbytes = C.c_void_p(), C.c_int64(0)
+    rc = load_library().sge_count_batch_ckpt(ctx, n, _p(tids), _p(pids),
+                                             C.byref(opts) if opts is not None else None,
+                                             C.cast(out, C.c_void_p), C.byref(ptr), C.byref(nbytes))
+    blob = _take_blob(ptr, nbytes)
+    if check and rc not in _STOPS:
+        _check(ctx, rc, "sge_count_batch_ckpt")
+    arr = np.ctypeslib.as_array(out)[:n] if n else np.zeros(0)
+    return int(rc), np.array(arr, copy=True), blob
+
+
+def sge_ckpt_info(blob: bytes):
+    """(pairs, unexplored frames) recorded in a checkpoint."""
+    npairs, nframes = C.c_int64(0), C.c_int64(0)
+    rc = load_library().sge_ckpt_info(blob, len(blob), C.byref(npairs), C.byref(nframes))
+    if rc != 0:
+        raise SgeError(int(rc), "malformed checkpoint")
+    return int(npairs.value), int(nframes.value)
+
+
+def sge_resume(ctx, blob: bytes, opts: sge_opts | None = None, check: bool = True):
+    """Continue from a checkpoint; returns (rc, rows with the counters so far, next checkpoint or None)."""
+    n, _ = sge_ckpt_info(blob)
+    out = (sge_result * max(n, 1))()
+    ptr, nbytes = C.c_void_p(), C.c_int64(0)
+    rc = load_library().sge_resume(ctx, blob, len(blob), C.byref(opts) if opts is not None else None,
+                                   C.cast(out, C.c_void_p), C.byref(ptr), C.byref(nbytes))
+    nxt = _take_blob(ptr, nbytes)
+    if check and rc not in _STOPS:
+        _check(ctx, rc, "sge_resume")
+    arr = np.ctypeslib.as_array(out)[:n] if n else np.zeros(0)
+    return int(rc), np.array(arr, copy=True), nxt
+
+
 def sge_enumerate(ctx, tid: int, pid: int, opts: sge_opts | None = None, check: bool = True):
     """(result dict, list of int32 arrays of shape (count, k) delivered to the sink)."""
     chunks = []
@@ -298,6 +360,12 @@ class Context:
 
     def count_batch(self, tids, pids, check=True, **opts):
         return sge_count_batch(self.h, tids, pids, make_opts(**opts), check=check)
+
+    def count_batch_ckpt(self, tids, pids, check=True, **opts):
+        return sge_count_batch_ckpt(self.h, tids, pids, make_opts(**opts), check=check)
+
+    def resume(self, blob, check=True, **opts):
+        return sge_resume(self.h, blob, make_opts(**opts), check=check)
 
     def enumerate(self, tid, pid, check=True, **opts):
         d, chunks = sge_enumerate(self.h, tid, pid, make_opts(**opts), check=check)

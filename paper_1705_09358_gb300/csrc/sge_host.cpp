@@ -229,11 +229,11 @@ struct Workspace {
     DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag;
     DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
-    DevBuf mbuf;
+    DevBuf mbuf, ckpt;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void release() {
         for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
-                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf})
+                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt})
             b->release();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -469,10 +469,20 @@ int pow2_at_least(int x) {
 
 // Run a homogeneous group of pairs (same directedness) through the whole
 // launch sequence on `st` with workspace `W`.
+// Resume input / checkpoint output of run_group (see sge_count_batch_ckpt).
+struct Resume {
+    const int32_t *frames = nullptr;   // frames of stride FRAME_HDR + kmax
+    long long n = 0;
+    int kmax = 0;
+};
+
 sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
                      const std::vector<int> &idx, const sge_opts &o, sge_result *out, bool enumerate,
-                     std::vector<int32_t> *match_rows, long long match_cap, bool serving) {
+                     std::vector<int32_t> *match_rows, long long match_cap, bool serving,
+                     const Resume *resume = nullptr, std::vector<int32_t> *ckpt_frames = nullptr,
+                     int *ckpt_kmax = nullptr) {
     const double t_start = now_ms();
+    if (ckpt_frames) ckpt_frames->clear();
     long long launches = 0;   // kernels launched by this call
     const int algo = o.algo;
     const int nj = (int)idx.size();
@@ -715,19 +725,34 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                 roots.push_back({q, 0, (int32_t)b, (int32_t)std::min<long long>(b + ROOT_CHUNK, len)});
         }
     }
-    const long long F0 = (long long)roots.size();
+    long long F0 = (long long)roots.size();
     long long F = 0;
     int cur = 0, depth = 0, fstride = FRAME_HDR;
     bool split_done = F0 == 0;
+    if (resume != nullptr) {
+        // continue from a checkpoint: its frames (mixed depths, stride FRAME_HDR + kmax) are the frontier
+        if (resume->kmax != kmax) return fail(ctx, SGE_ERR_ARG, "checkpoint does not match these pairs");
+        fstride = FRAME_HDR + kmax;
+        F = resume->n;
+        if (F > 0) {
+            CK(W.front[0].ensure((size_t)F * fstride * 4), "alloc frontier");
+            CK(cudaMemcpyAsync(W.front[0].p, resume->frames, (size_t)F * fstride * 4, cudaMemcpyHostToDevice, st),
+               "upload checkpoint frames");
+        }
+        split_done = true;
+    }
     const int max_levels = std::max(0, std::min(o.split_depth > 0 ? o.split_depth : INT_MAX, kmax - 1));
-    if (!split_done) {
+    if (!split_done && resume == nullptr) {
         // the whole split as one cooperative launch.  Auto depth, CSR kernel: breadth-first
         // for as long as the next level fits the frontier budget (deep, narrow searches are
         // far cheaper level by level than depth-first, and the split tests candidates the way
         // the CSR kernel does).  Bitset kernel: stop at the frame target, since its
         // word-parallel expansion beats the split's per-candidate tests on dense targets.
+        // A state budget or time limit is enforced by the search kernel, so with either
+        // set the split also stops at the frame target and the search does the bulk.
+        const bool limited = o.state_budget > 0 || o.time_limit_ms > 0;
         const long long target = o.split_depth > 0 ? LLONG_MAX
-                                 : kernel == SGE_KERNEL_BITSET ? target_frames : (long long)INT_MAX;
+                                 : (kernel == SGE_KERNEL_BITSET || limited) ? target_frames : (long long)INT_MAX;
         const long long cap_ints = std::max<long long>(F0 * FRAME_HDR, FRONTIER_MAX_INTS);
         CK(W.front[0].ensure((size_t)cap_ints * 4), "alloc frontier");
         CK(W.front[1].ensure((size_t)cap_ints * 4), "alloc frontier");
@@ -765,7 +790,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             (void)cudaGetLastError();   // cooperative launch refused: split level by level below
         }
     }
-    if (!split_done) {
+    if (!split_done && resume == nullptr) {
         fstride = FRAME_HDR;
         std::vector<int32_t> f0;
         for (const auto &r : roots) f0.insert(f0.end(), r.begin(), r.end());
@@ -860,6 +885,18 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             CK(W.slab.ensure(slab_bytes), "alloc search slab");
             C.slab = W.slab.as<uint64_t>();
         }
+        const int cs = FRAME_HDR + kmax;   // checkpoint frame stride
+        if (ckpt_frames != nullptr) {
+            // each warp dumps at most two range frames per level
+            const long long cap = max_grid * search_warps_per_block() * 2 * kmax;
+            const size_t bytes = (size_t)cap * cs * 4;
+            CK(W.ckpt.ensure(bytes + 64), "alloc checkpoint");
+            C.ckpt = W.ckpt.as<int32_t>();
+            C.ckpt_cap = cap;
+            C.ckpt_stride = cs;
+            C.ckpt_n = reinterpret_cast<unsigned long long *>(W.ckpt.as<char>() + bytes);
+            CK(cudaMemsetAsync(C.ckpt_n, 0, 8, st), "clear checkpoint");
+        }
         CK(cudaEventRecord(W.ev0, st), "event record");
         CK(launch_search(kfam, W.jobs.as<JobDesc>(), C, kmax, nwl, directed ? 1 : 0, o.blocks_per_sm, max_grid, &grid,
                          st), "search launch");
@@ -874,6 +911,39 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         if (trace_on())
             std::fprintf(stderr, "[sge] search grid %d frames %lld kernel %.3f ms status %d donations %llu\n", grid,
                          nfront, kernel_ms, status, dn);
+        if (ckpt_frames != nullptr && (status == SGE_ERR_BUDGET || status == SGE_ERR_TIMEOUT ||
+                                       status == SGE_ERR_CANCELLED)) {
+            // unexplored work = the warps' dumps + frontier frames never taken + queued frames
+            unsigned long long hc[4] = {0, 0, 0, 0}, nd = 0;
+            CK(cudaMemcpyAsync(hc, c64, sizeof(hc), cudaMemcpyDeviceToHost, st), "read control");
+            CK(cudaMemcpyAsync(&nd, C.ckpt_n, 8, cudaMemcpyDeviceToHost, st), "read checkpoint count");
+            CK(cudaStreamSynchronize(st), "checkpoint sync");
+            if ((long long)nd > C.ckpt_cap) return fail(ctx, SGE_ERR_OOM, "checkpoint larger than its buffer");
+            std::vector<int32_t> &outf = *ckpt_frames;
+            outf.clear();
+            // n frames of `stride` ints, `pitch` ints apart, into frames of cs ints
+            auto take = [&](const int32_t *dev, long long n, int stride, long long pitch) -> cudaError_t {
+                if (n <= 0) return cudaSuccess;
+                const size_t at = outf.size();
+                outf.resize(at + (size_t)n * cs, 0);
+                return cudaMemcpy2DAsync(outf.data() + at, (size_t)cs * 4, dev, (size_t)pitch * 4,
+                                         (size_t)std::min(stride, cs) * 4, (size_t)n, cudaMemcpyDeviceToHost, st);
+            };
+            CK(take(C.ckpt, (long long)nd, cs, cs), "read checkpoint frames");
+            // frontier frames of this shard never taken (frame i of the shard is frame i*count+index)
+            const long long taken = std::min<long long>((long long)hc[0], nfront);
+            CK(take(C.front + (taken * shard_count + shard_index) * (long long)fstride, nfront - taken, fstride,
+                    (long long)fstride * shard_count), "read frontier");
+            // queued frames never taken: cells [head, tail) of the ring
+            for (unsigned long long t = hc[1]; t < hc[2];) {
+                const unsigned long long cell = t % POOL_CELLS;
+                const unsigned long long n = std::min<unsigned long long>(hc[2] - t, POOL_CELLS - cell);
+                CK(take(C.pool + (size_t)cell * POOL_STRIDE, (long long)n, POOL_STRIDE, POOL_STRIDE), "read queue");
+                t += n;
+            }
+            CK(cudaStreamSynchronize(st), "checkpoint sync");
+            if (ckpt_kmax) *ckpt_kmax = kmax;
+        }
     }
     std::vector<unsigned long long> ctr((size_t)nj * 6);
     CK(cudaMemcpyAsync(ctr.data(), W.ctr.p, (size_t)nj * 6 * 8, cudaMemcpyDeviceToHost, st), "read counters");
@@ -914,10 +984,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     return SGE_OK;
 }
 
-sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
-                     const sge_opts *opts, sge_result *out, bool enumerate, std::vector<int32_t> *rows,
-                     long long cap, bool serving = false) {
-    sge_opts o;
+// Options with defaults applied, checked, and the pairs split by directedness.
+sge_status prepare_pairs(sge_ctx *ctx, const std::vector<PairReq> &reqs, const sge_opts *opts, sge_opts &o,
+                         std::vector<int> &und, std::vector<int> &dir) {
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     if (o.time_limit_ms <= 0) {
@@ -929,7 +998,8 @@ sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     if (o.kernel < 0 || o.kernel > 2) return fail(ctx, SGE_ERR_ARG, "unknown kernel family");
     if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count))
         return fail(ctx, SGE_ERR_ARG, "shard index out of range");
-    std::vector<int> und, dir;
+    und.clear();
+    dir.clear();
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         for (size_t i = 0; i < reqs.size(); ++i) {
@@ -946,9 +1016,234 @@ sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             (ti->second->directed ? dir : und).push_back((int)i);
         }
     }
-    sge_status rc = SGE_OK;
+    return SGE_OK;
+}
+
+sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
+                     const sge_opts *opts, sge_result *out, bool enumerate, std::vector<int32_t> *rows,
+                     long long cap, bool serving = false) {
+    sge_opts o;
+    std::vector<int> und, dir;
+    sge_status rc = prepare_pairs(ctx, reqs, opts, o, und, dir);
+    if (rc != SGE_OK) return rc;
     if (!und.empty()) rc = run_group(ctx, W, st, reqs, und, o, out, enumerate, rows, cap, serving);
     if (rc == SGE_OK && !dir.empty()) rc = run_group(ctx, W, st, reqs, dir, o, out, enumerate, rows, cap, serving);
+    return rc;
+}
+
+// ------------------------------------------------------------ checkpoints
+//
+// A checkpoint is one host blob (little-endian, all fields naturally aligned):
+//   header   u64 magic, i32 version, i32 algo, i64 npairs, i32 ngroups, i32 0
+//   pairs    npairs x {i32 target id, i32 pattern id, i32 n_t, i32 k}
+//   counters npairs x {u64 matches, states, nodes, hash}   (so far, all calls)
+//   groups   ngroups x {i32 kmax, i32 npairs_g, i64 nframes,
+//                       npairs_g x i32 pair index (+ one i32 pad if odd),
+//                       nframes x (4 + kmax) i32 frames}
+// A frame is [job, depth (| FRAME_COUNTED), begin, end, M_0 .. M_{depth-1}]:
+// job indexes the group's pair list, M the images of the first depth
+// positions of the pair's search order.
+constexpr uint64_t CKPT_MAGIC = 0x3154504B43454753ull;   // "SGECKPT1"
+constexpr int32_t CKPT_VERSION = 1;
+
+struct CkptGroup {
+    std::vector<int> idx;          // pair indices, in job order
+    int kmax = 0;
+    std::vector<int32_t> frames;   // stride FRAME_HDR + kmax
+};
+
+struct CkptState {
+    int algo = 0;
+    std::vector<PairReq> reqs;
+    std::vector<int32_t> nt, k;
+    std::vector<uint64_t> ctr;     // 4 per pair
+    std::vector<CkptGroup> groups;
+};
+
+template <class T>
+void put(std::vector<unsigned char> &b, const T &v) {
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(&v);
+    b.insert(b.end(), p, p + sizeof(T));
+}
+
+std::vector<unsigned char> ckpt_write(const CkptState &S) {
+    std::vector<unsigned char> b;
+    put(b, CKPT_MAGIC);
+    put(b, CKPT_VERSION);
+    put(b, (int32_t)S.algo);
+    put(b, (int64_t)S.reqs.size());
+    put(b, (int32_t)S.groups.size());
+    put(b, (int32_t)0);
+    for (size_t i = 0; i < S.reqs.size(); ++i) {
+        put(b, S.reqs[i].tid);
+        put(b, S.reqs[i].pid);
+        put(b, S.nt[i]);
+        put(b, S.k[i]);
+    }
+    for (uint64_t v : S.ctr) put(b, v);
+    for (const CkptGroup &g : S.groups) {
+        const int stride = FRAME_HDR + g.kmax;
+        put(b, (int32_t)g.kmax);
+        put(b, (int32_t)g.idx.size());
+        put(b, (int64_t)(g.frames.size() / stride));
+        for (int i : g.idx) put(b, (int32_t)i);
+        if (g.idx.size() & 1) put(b, (int32_t)0);
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(g.frames.data());
+        b.insert(b.end(), p, p + g.frames.size() * 4);
+    }
+    return b;
+}
+
+// Parses and checks a blob against the context (ids loaded, sizes unchanged,
+// every frame within its pair's pattern and target).  Returns an error
+// message, empty on success.
+std::string ckpt_read(sge_ctx *ctx, const unsigned char *b, long long bytes, CkptState &S) {
+    long long at = 0;
+    auto get = [&](void *dst, long long n) {
+        if (n < 0 || at + n > bytes) return false;
+        std::memcpy(dst, b + at, (size_t)n);
+        at += n;
+        return true;
+    };
+    uint64_t magic = 0;
+    int32_t version = 0, algo = 0, ngroups = 0, pad = 0;
+    int64_t npairs = 0;
+    if (!get(&magic, 8) || magic != CKPT_MAGIC) return "not a checkpoint";
+    if (!get(&version, 4) || version != CKPT_VERSION) return "unsupported checkpoint version";
+    if (!get(&algo, 4) || algo < SGE_RI || algo > SGE_RIDS_SI_FC) return "bad algo in checkpoint";
+    if (!get(&npairs, 8) || npairs < 0 || npairs > bytes / 48) return "bad pair count in checkpoint";
+    if (!get(&ngroups, 4) || ngroups < 0 || ngroups > 2 || !get(&pad, 4)) return "bad group count in checkpoint";
+    S.algo = algo;
+    S.reqs.resize((size_t)npairs);
+    S.nt.resize((size_t)npairs);
+    S.k.resize((size_t)npairs);
+    S.ctr.resize((size_t)npairs * 4);
+    std::vector<char> dir((size_t)npairs, 0);
+    for (int64_t i = 0; i < npairs; ++i) {
+        int32_t f[4];
+        if (!get(f, 16)) return "truncated checkpoint";
+        S.reqs[i] = {f[0], f[1]};
+        S.nt[i] = f[2];
+        S.k[i] = f[3];
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto ti = ctx->targets.find(f[0]);
+        auto pi = ctx->patterns.find(f[1]);
+        if (ti == ctx->targets.end() || pi == ctx->patterns.end()) return "checkpoint names an unknown target or pattern";
+        if (ti->second->n != f[2] || pi->second->k != f[3]) return "checkpoint target or pattern size differs";
+        dir[i] = ti->second->directed ? 1 : 0;
+    }
+    if (!get(S.ctr.data(), npairs * 32)) return "truncated checkpoint";
+    std::vector<char> seen((size_t)npairs, 0);
+    for (int32_t g = 0; g < ngroups; ++g) {
+        CkptGroup G;
+        int32_t kmax = 0, np = 0;
+        int64_t nf = 0;
+        if (!get(&kmax, 4) || !get(&np, 4) || !get(&nf, 8)) return "truncated checkpoint";
+        if (kmax < 1 || kmax > KMAX || np < 1 || np > npairs || nf < 0) return "bad checkpoint group";
+        G.kmax = kmax;
+        G.idx.resize((size_t)np);
+        if (!get(G.idx.data(), 4ll * np)) return "truncated checkpoint";
+        if (np & 1) { int32_t z; if (!get(&z, 4)) return "truncated checkpoint"; }
+        int gk = 1;
+        for (int q = 0; q < np; ++q) {
+            const int i = G.idx[q];
+            if (i < 0 || i >= npairs || seen[i]) return "bad checkpoint group";
+            if (dir[i] != dir[G.idx[0]]) return "checkpoint group mixes directedness";
+            seen[i] = 1;
+            if (S.k[i] <= S.nt[i]) gk = std::max(gk, S.k[i]);
+        }
+        if (gk != kmax) return "checkpoint group kmax differs from its pairs";
+        const int stride = FRAME_HDR + kmax;
+        if (nf > (bytes - at) / (4ll * stride)) return "truncated checkpoint";
+        G.frames.resize((size_t)nf * stride);
+        if (!get(G.frames.data(), nf * 4ll * stride)) return "truncated checkpoint";
+        for (int64_t f = 0; f < nf; ++f) {
+            const int32_t *fr = G.frames.data() + f * stride;
+            const int j = fr[0];
+            if (j < 0 || j >= np) return "checkpoint frame names no pair";
+            const int i = G.idx[j];
+            const int depth = fr[1] & FRAME_DEPTH_MASK;
+            // (a counted range never lies on the last position: its matches are counted at once)
+            if ((fr[1] & ~(FRAME_DEPTH_MASK | FRAME_COUNTED)) != 0 || S.k[i] > S.nt[i] || depth >= S.k[i] ||
+                ((fr[1] & FRAME_COUNTED) && (depth >= S.k[i] - 1 || fr[2] < 0)))
+                return "bad checkpoint frame depth";
+            if (fr[2] < -1 || (fr[2] >= 0 && fr[3] < fr[2])) return "bad checkpoint frame range";
+            for (int t = 0; t < depth; ++t)
+                if (fr[FRAME_HDR + t] < 0 || fr[FRAME_HDR + t] >= S.nt[i]) return "bad checkpoint frame image";
+        }
+        S.groups.push_back(std::move(G));
+    }
+    if (at != bytes) return "checkpoint has trailing bytes";
+    return std::string();
+}
+
+bool stop_status(sge_status rc) {
+    return rc == SGE_ERR_BUDGET || rc == SGE_ERR_TIMEOUT || rc == SGE_ERR_CANCELLED;
+}
+
+// Runs S's groups (all of them from the start, or each group's frames when
+// resuming), adds the counters to S.ctr, and leaves in each group the frames
+// still unexplored.  Returns OK when nothing is left, else the first stop
+// status (other errors end the call at once).
+sge_status run_ckpt(sge_ctx *ctx, const sge_opts &o, CkptState &S, bool resume, sge_result *out) {
+    sge_status first_stop = SGE_OK;
+    std::vector<sge_result> tmp(S.reqs.size());
+    for (size_t i = 0; i < S.reqs.size(); ++i) {
+        std::memset(&out[i], 0, sizeof(sge_result));
+        out[i].status = 0;
+    }
+    for (CkptGroup &G : S.groups) {
+        if (G.kmax == 0) {   // the group's largest searchable pattern, as run_group sizes frames
+            G.kmax = 1;
+            for (int i : G.idx)
+                if (S.k[i] <= S.nt[i]) G.kmax = std::max(G.kmax, (int)S.k[i]);
+        }
+        if (resume && G.frames.empty()) continue;
+        Resume R;
+        R.frames = G.frames.data();
+        R.n = (long long)(G.frames.size() / (FRAME_HDR + G.kmax));
+        R.kmax = G.kmax;
+        std::vector<int32_t> left;
+        int kmax = G.kmax;
+        sge_status rc = run_group(ctx, ctx->ws, ctx->stream, S.reqs, G.idx, o, tmp.data(), false, nullptr, 0, false,
+                                  resume ? &R : nullptr, &left, &kmax);
+        if (rc != SGE_OK && !stop_status(rc)) return rc;
+        if (rc != SGE_OK && first_stop == SGE_OK) first_stop = rc;
+        for (int i : G.idx) {
+            out[i] = tmp[i];
+            S.ctr[4 * (size_t)i + 0] += tmp[i].matches;
+            S.ctr[4 * (size_t)i + 1] += tmp[i].states;
+            S.ctr[4 * (size_t)i + 2] += tmp[i].nodes;
+            S.ctr[4 * (size_t)i + 3] += tmp[i].hash;
+        }
+        G.kmax = kmax;
+        G.frames.swap(left);   // empty when the group finished
+    }
+    for (size_t i = 0; i < S.reqs.size(); ++i) {
+        out[i].matches = S.ctr[4 * i + 0];
+        out[i].states = S.ctr[4 * i + 1];
+        out[i].nodes = S.ctr[4 * i + 2];
+        out[i].hash = S.ctr[4 * i + 3];
+    }
+    if (first_stop != SGE_OK) {
+        // a stop with nothing left to do (all the work fit before it) is a finished search
+        bool left = false;
+        for (const CkptGroup &G : S.groups) left = left || !G.frames.empty();
+        if (!left) first_stop = SGE_OK;
+    }
+    return first_stop;
+}
+
+sge_status ckpt_hand_out(sge_ctx *ctx, const CkptState &S, sge_status rc, void **ckpt, int64_t *ckpt_bytes) {
+    *ckpt = nullptr;
+    *ckpt_bytes = 0;
+    if (rc == SGE_OK) return SGE_OK;
+    const std::vector<unsigned char> b = ckpt_write(S);
+    void *p = std::malloc(b.size());
+    if (!p) return fail(ctx, SGE_ERR_OOM, "checkpoint blob allocation failed");
+    std::memcpy(p, b.data(), b.size());
+    *ckpt = p;
+    *ckpt_bytes = (int64_t)b.size();
     return rc;
 }
 
@@ -1162,6 +1457,100 @@ sge_status sge_count_batch(sge_ctx *ctx, int64_t npairs, const int32_t *target_i
     if (npairs == 0) return SGE_OK;
     return run_pairs(ctx, ctx->ws, ctx->stream, reqs, opts, out, false, nullptr, 0);
 }
+
+sge_status sge_count_batch_ckpt(sge_ctx *ctx, int64_t npairs, const int32_t *target_ids, const int32_t *pattern_ids,
+                                const sge_opts *opts, sge_result *out, void **ckpt, int64_t *ckpt_bytes) {
+    if (!ctx || !out || !ckpt || !ckpt_bytes || npairs < 0 || (npairs > 0 && (!target_ids || !pattern_ids)))
+        return SGE_ERR_ARG;
+    *ckpt = nullptr;
+    *ckpt_bytes = 0;
+    if (npairs > INT32_MAX / 8) return fail(ctx, SGE_ERR_ARG, "too many pairs");
+    if (npairs == 0) return SGE_OK;
+    cudaSetDevice(ctx->device);
+    *ctx->cancel_host = 0;
+    CkptState S;
+    S.reqs.resize((size_t)npairs);
+    for (int64_t i = 0; i < npairs; ++i) S.reqs[i] = {target_ids[i], pattern_ids[i]};
+    sge_opts o;
+    std::vector<int> und, dir;
+    sge_status rc = prepare_pairs(ctx, S.reqs, opts, o, und, dir);
+    if (rc != SGE_OK) return rc;
+    S.algo = o.algo;
+    S.nt.resize((size_t)npairs);
+    S.k.resize((size_t)npairs);
+    S.ctr.assign((size_t)npairs * 4, 0);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (int64_t i = 0; i < npairs; ++i) {
+            S.nt[i] = ctx->targets.at(S.reqs[i].tid)->n;
+            S.k[i] = ctx->patterns.at(S.reqs[i].pid)->k;
+        }
+    }
+    for (std::vector<int> *grp : {&und, &dir})
+        if (!grp->empty()) {
+            CkptGroup G;
+            G.idx = *grp;
+            S.groups.push_back(std::move(G));
+        }
+    rc = run_ckpt(ctx, o, S, false, out);
+    return ckpt_hand_out(ctx, S, rc, ckpt, ckpt_bytes);
+}
+
+sge_status sge_resume(sge_ctx *ctx, const void *ckpt, int64_t ckpt_bytes, const sge_opts *opts, sge_result *out,
+                      void **next, int64_t *next_bytes) {
+    if (!ctx || !ckpt || ckpt_bytes <= 0 || !out || !next || !next_bytes) return SGE_ERR_ARG;
+    *next = nullptr;
+    *next_bytes = 0;
+    cudaSetDevice(ctx->device);
+    *ctx->cancel_host = 0;
+    CkptState S;
+    const std::string err = ckpt_read(ctx, static_cast<const unsigned char *>(ckpt), ckpt_bytes, S);
+    if (!err.empty()) return fail(ctx, SGE_ERR_ARG, err);
+    sge_opts o;
+    std::vector<int> und, dir;
+    sge_opts oi;
+    std::memset(&oi, 0, sizeof(oi));
+    if (opts) oi = *opts;
+    oi.algo = S.algo;          // the frames follow the checkpoint's variant
+    oi.shard_count = 0;        // and hold only this shard's work already
+    oi.shard_index = 0;
+    sge_status rc = prepare_pairs(ctx, S.reqs, &oi, o, und, dir);
+    if (rc != SGE_OK) return rc;
+    rc = run_ckpt(ctx, o, S, true, out);
+    return ckpt_hand_out(ctx, S, rc, next, next_bytes);
+}
+
+sge_status sge_ckpt_info(const void *ckpt, int64_t ckpt_bytes, int64_t *npairs, int64_t *nframes) {
+    if (!ckpt || ckpt_bytes < 32 || !npairs || !nframes) return SGE_ERR_ARG;
+    const unsigned char *b = static_cast<const unsigned char *>(ckpt);
+    uint64_t magic = 0;
+    int32_t version = 0, ngroups = 0;
+    int64_t np = 0;
+    std::memcpy(&magic, b, 8);
+    std::memcpy(&version, b + 8, 4);
+    std::memcpy(&np, b + 16, 8);
+    std::memcpy(&ngroups, b + 24, 4);
+    if (magic != CKPT_MAGIC || version != CKPT_VERSION || np < 0 || ngroups < 0 || ngroups > 2) return SGE_ERR_ARG;
+    long long at = 32 + np * 48;
+    long long frames = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        int32_t kmax = 0, n = 0;
+        int64_t nf = 0;
+        if (at + 16 > ckpt_bytes) return SGE_ERR_ARG;
+        std::memcpy(&kmax, b + at, 4);
+        std::memcpy(&n, b + at + 4, 4);
+        std::memcpy(&nf, b + at + 8, 8);
+        if (kmax < 1 || kmax > KMAX || n < 0 || nf < 0) return SGE_ERR_ARG;
+        at += 16 + 4ll * (n + (n & 1)) + nf * 4ll * (FRAME_HDR + kmax);
+        frames += nf;
+    }
+    if (at != ckpt_bytes) return SGE_ERR_ARG;
+    *npairs = np;
+    *nframes = frames;
+    return SGE_OK;
+}
+
+void sge_free(void *p) { std::free(p); }
 
 sge_status sge_enumerate(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, const sge_opts *opts,
                          sge_match_sink sink, void *user, sge_result *out) {

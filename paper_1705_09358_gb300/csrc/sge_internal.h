@@ -23,6 +23,12 @@ namespace sge {
 constexpr int KMAX = 128;            // largest pattern handled by the kernels
 constexpr int FRAME_HDR = 4;         // job, depth, begin, end
 constexpr int POOL_STRIDE = FRAME_HDR + KMAX;
+// Flag in a frame's depth word: the frame is the remainder [begin, end) of a
+// node's candidate range whose accepted nodes (and the node's states) were
+// already counted when the candidates were first tested; it only re-derives
+// the survivors to search below them.  Checkpoints write such frames.
+constexpr int FRAME_COUNTED = 1 << 16;
+constexpr int FRAME_DEPTH_MASK = FRAME_COUNTED - 1;
 
 // PosInfo.flags
 constexpr int POS_IN_ROW = 1;        // candidates come from the parent's in-row (directed)
@@ -127,6 +133,10 @@ struct SearchCtl {
     unsigned long long donate_ns; // ... or per this much device time, whichever comes first
     unsigned long long idle_exit_ns; // a warp idle this long exits (0 = wait for the end)
     uint64_t *slab;             // bitset kernel: per-warp level bitsets (search_slab_bytes)
+    int32_t *ckpt;              // checkpoint: on a stop, warps dump their unexplored work here
+    long long ckpt_cap;         // ... up to this many frames of ckpt_stride ints
+    int32_t ckpt_stride;        // FRAME_HDR + kmax
+    unsigned long long *ckpt_n; // frames dumped (may exceed ckpt_cap: then the dump is incomplete)
 };
 
 // ------------------------------------------------------------ launchers

@@ -760,7 +760,36 @@ __device__ bool push_frame(const SearchCtl &C, int j, int depth, int beg, int en
 
 struct Frame {
     int job, depth, beg, end;
+    bool counted;   // FRAME_COUNTED: the range's accepted nodes and states are already counted
 };
+
+// Warp-collective: append range frame [j, depth (| FRAME_COUNTED), beg, end,
+// M[0..depth-1]] to the checkpoint.  Every warp dumps at most two frames per
+// level, so a buffer of 2 * kmax frames per warp never overflows.
+__device__ void ckpt_push(const SearchCtl &C, int j, int depth, bool counted, int beg, int end, const int *M) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(C.ckpt_n, 1ull);
+    slot = __shfl_sync(FULL, slot, 0);
+    if ((long long)slot >= C.ckpt_cap) return;
+    int32_t *cell = C.ckpt + (size_t)slot * C.ckpt_stride;
+    if (lane == 0) { cell[0] = j; cell[1] = depth | (counted ? FRAME_COUNTED : 0); cell[2] = beg; cell[3] = end; }
+    for (int i = lane; i < depth; i += 32) cell[FRAME_HDR + i] = M[i];
+    __syncwarp();
+}
+
+// First index in ascending a[0..n) whose value is >= x (lane 0 searches, all lanes get it).
+__device__ int lower_bound_warp(const int32_t *a, int n, int x) {
+    int lo = 0;
+    if ((threadIdx.x & 31) == 0) {
+        int hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+        }
+    }
+    return __shfl_sync(FULL, lo, 0);
+}
 
 // Warp-collective: take the next frame (frontier first, then the queue) and
 // copy its images into M.  Waits (bounded) while other warps still hold work.
@@ -820,7 +849,9 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
         __syncwarp();
         src = C.pool + (size_t)(idx % C.pcap) * POOL_STRIDE;
     }
-    fr.job = src[0]; fr.depth = src[1]; fr.beg = src[2]; fr.end = src[3];
+    const int dw = src[1];
+    fr.job = src[0]; fr.depth = dw & FRAME_DEPTH_MASK; fr.counted = (dw & FRAME_COUNTED) != 0;
+    fr.beg = src[2]; fr.end = src[3];
     for (int i = lane; i < fr.depth; i += 32) M[i] = src[FRAME_HDR + i];
     __syncwarp();
     if (kind == 2 && lane == 0) {
@@ -892,6 +923,7 @@ struct LvCsr {
     int cur, end;            // unscanned candidates [cur, end)
     unsigned mask;           // survivors of the last scanned chunk, not yet descended
     int cbase;               // index of that chunk's first candidate
+    int len;                 // the node's raw candidate count (its states, counted at index 0)
 };
 
 __host__ __device__ __forceinline__ size_t csr_smem_per_warp(int kmax) {
@@ -986,9 +1018,11 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             __syncwarp();
         }
         const int k = B.k, d0 = fr.depth;
+        // a counted frame re-tests its range at level d0 without counting it again
+        const int quiet = fr.counted ? d0 : -1;
         unsigned long long st = 0, nd = 0, mt = 0, hs = 0;
-        // set up level `lvl` (positions 0..lvl-1 assigned); returns the raw candidate count
-        auto setup = [&](int l, int beg, int endv) -> int {
+        // set up level `l` (positions 0..l-1 assigned)
+        auto setup = [&](int l, int beg, int endv) {
             const PosC p = tab[l];
             int b0, len;
             if (p.par >= 0) {
@@ -1007,14 +1041,14 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             int cur = 0, end = len;
             if (beg >= 0) { cur = beg; end = min(endv, len); }
             __syncwarp();
-            if (lane == 0) { lv[l].base = b0; lv[l].cur = cur; lv[l].end = end; lv[l].mask = 0; lv[l].cbase = 0; }
+            if (lane == 0) {
+                lv[l].base = b0; lv[l].cur = cur; lv[l].end = end; lv[l].mask = 0; lv[l].cbase = 0; lv[l].len = len;
+            }
             __syncwarp();
-            return len;
         };
-        {
-            const int len = setup(d0, fr.beg, fr.end);
-            if (fr.beg <= 0) st += (unsigned long long)len;   // a node's first (or only) range counts its states
-        }
+        // a node's states are counted when its candidate 0 is scanned, so every split of
+        // its candidate range (range frames, donations, checkpoints) counts them exactly once
+        setup(d0, fr.beg, fr.end);
         int lvl = d0;
         bool stopped = false;
         for (;;) {
@@ -1035,7 +1069,8 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                         const int rem = L.end - L.cur;
                         if (rem >= 64) {
                             const int mid = L.cur + ((rem / 2 + 31) & ~31);
-                            if (push_frame(C, fr.job, l, mid, L.end, M, l, -1)) {
+                            if (push_frame(C, fr.job, l | (l == quiet ? FRAME_COUNTED : 0), mid, L.end, M, l,
+                                           -1)) {
                                 __syncwarp();
                                 if (lane == 0) L.end = mid;
                                 __syncwarp();
@@ -1072,6 +1107,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                     continue;
                 }
                 const int cnt = min(32, end - cur);
+                if (cur == 0 && lvl != quiet) st += (unsigned long long)L.len;
                 bool ok = false;
                 int c = -1;
                 if (lane < cnt) {
@@ -1080,7 +1116,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                     ok = csr_feasible<DIR>(B, p, lvl, c, (src && p.par >= 0) ? e : -1, M);
                 }
                 unsigned bal = __ballot_sync(FULL, ok);
-                nd += __popc(bal);
+                if (lvl != quiet) nd += __popc(bal);
                 if (lvl == k - 1) {
                     mt += __popc(bal);
                     if (bal) {
@@ -1110,7 +1146,22 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             }
             __syncwarp();
             ++lvl;
-            st += (unsigned long long)setup(lvl, -1, 0);
+            setup(lvl, -1, 0);
+        }
+        if (stopped && C.ckpt != nullptr) {
+            // checkpoint, per level: the part of the current chunk from its lowest pending
+            // survivor on (already counted; survivors are taken lowest first), then the
+            // unscanned rest of the range (counted only if the frame itself was)
+            for (int l = d0; l <= lvl; ++l) {
+                const LvCsr L = lv[l];
+                const int cb = L.mask ? L.cbase + __ffs(L.mask) - 1 : L.cur;
+                if (l == quiet) {
+                    if (cb < L.end) ckpt_push(C, fr.job, l, true, cb, L.end, M);
+                } else {
+                    if (cb < L.cur) ckpt_push(C, fr.job, l, true, cb, L.cur, M);
+                    if (L.cur < L.end) ckpt_push(C, fr.job, l, false, L.cur, L.end, M);
+                }
+            }
         }
         hs = warp_sum(hs);
         if (lane == 0) {
@@ -1415,11 +1466,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             else if (lst) { vlo = __ldg(lst + b0 + fr.beg); vhi = __ldg(lst + b0 + e - 1); }
             else { vlo = fr.beg; vhi = e - 1; }
         }
-        const bool count_len = fr.beg <= 0;
+        const bool count_len = fr.beg <= 0 && !fr.counted;
         const bool leaf0 = d0 == k - 1;
         const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, d0, leaf0, st, hs, ab, vlo, vhi, count_len)
                                    : bits_expand<NWL>(B, J, W, d0, leaf0, st, hs, ab);
-        nd += c0;
+        if (!fr.counted) nd += c0;
         if (leaf0) {
             mt += c0;
         } else {
@@ -1473,6 +1524,39 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     ++lvl;
                     if (lane == 0) M[lvl] = -1;
                     __syncwarp();
+                }
+            }
+            if (stopped && C.ckpt != nullptr) {
+                // checkpoint: the pending survivors of each level as one counted range frame.
+                // They are a contiguous run of the level's ascending survivors (a short list is
+                // taken from its top, a spilled bitset from its lowest bit), so one index range
+                // of the level's candidate list holds exactly them among the feasible candidates.
+                for (int l = d0; l <= lvl; ++l) {
+                    const PosB p = W.tab[l];
+                    const int32_t *lst = nullptr;
+                    int len = J.t.n;
+                    if (p.par >= 0) {
+                        const int a = M[p.par];
+                        const int b0 = __ldg(J.t.rowptr + a);
+                        lst = J.t.col + b0;
+                        len = __ldg(J.t.rowptr + a + 1) - b0;
+                    } else if (J.flags & JOB_RIDS) {
+                        lst = J.ulist + J.pos[l].uoff;
+                        len = J.pos[l].ucnt;
+                    }
+                    int lo = 0, hi = len;   // the level's own range
+                    if (l == d0 && fr.beg >= 0) { lo = fr.beg; hi = min(fr.end, len); }
+                    const int c = W.lcnt[l];
+                    if (c == 0) continue;
+                    if (c != LIST_SPILLED) {
+                        const int vmax = W.lst[l * LIST_CAP + c - 1];
+                        hi = lst ? lower_bound_warp(lst, len, vmax + 1) : vmax + 1;
+                    } else {
+                        const int vmin = bits_next<NWL>(W, l);
+                        if (vmin < 0) continue;
+                        lo = lst ? lower_bound_warp(lst, len, vmin) : vmin;
+                    }
+                    if (lo < hi) ckpt_push(C, fr.job, l, true, lo, hi, M);
                 }
             }
         }

@@ -61,3 +61,30 @@ def test_product_does_not_import_oracle():
                 with open(os.path.join(dirpath, fn)) as f:
                     src = f.read()
                 assert "import oracle" not in src and "from oracle" not in src and "sge_oracle" not in src, fn
+
+
+def _blob(npairs=3, groups=((2, (0, 2), 5), (1, (1,), 0))):
+    """A checkpoint blob laid out as include/sge.h documents it."""
+    import struct
+    b = struct.pack("<Qiiqii", 0x3154504B43454753, 1, 3, npairs, len(groups), 0)
+    for i in range(npairs):
+        b += struct.pack("<iiii", 10 + i, 20 + i, 100, 2)
+    b += b"\0" * (32 * npairs)
+    for kmax, idx, nf in groups:
+        b += struct.pack("<iiq", kmax, len(idx), nf)
+        b += struct.pack(f"<{len(idx)}i", *idx) + (b"\0" * 4 if len(idx) & 1 else b"")
+        for f in range(nf):
+            b += struct.pack(f"<{4 + kmax}i", 0, 1, -1, -1, f, *([0] * (kmax - 1)))
+    return b
+
+
+def test_checkpoint_blob_info():
+    # host-only parsing of the documented blob layout: no GPU involved
+    from paper_1705_09358_gb300 import build, sge_ckpt_info, SgeError
+    build.build()
+    blob = _blob()
+    assert sge_ckpt_info(blob) == (3, 5)
+    assert sge_ckpt_info(_blob(groups=())) == (3, 0)
+    for bad in (blob[:-4], blob + b"\0" * 4, b"\0" * len(blob), blob[:20]):
+        with pytest.raises(SgeError):
+            sge_ckpt_info(bad)
