@@ -358,12 +358,14 @@ def serving_latency(E, n_queries: int = 1000) -> dict:
     res = [E.serve_poll(tk) for tk in tickets]
     lat = np.array([r["latency_ms"] for r in res])
     bad = sum(1 for r in res if r["status"] != 0)
+    bad_status = sorted({int(r["status"]) for r in res if r["status"] != 0})
     served_states = sum(r["states"] for r in res)
     return {"workload": f"cl100k: Chung-Lu n=100,000 target, first {n} of the 5000 queries (8-128 vertices), RI",
             "queries": n, "arrival": "Poisson", "offered_qps": lam,
             "offered_load": "0.8 x serving saturation throughput", "saturation_qps": n / t_sat,
             "batched_qps": n / tb, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "errors": bad, "served_states_per_s": served_states / makespan,
+            "mean_ms": float(lat.mean()), "errors": bad, "error_statuses": bad_status,
+            "served_states_per_s": served_states / makespan,
             "makespan_s": makespan, "batched_states_per_s": total_states / tb,
             "sequential_per_query_states_per_s": s_seq / t_seq,
             "served_vs_sequential": (served_states / makespan) / (s_seq / t_seq)}

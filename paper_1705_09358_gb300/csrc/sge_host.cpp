@@ -40,8 +40,14 @@ constexpr int POOL_CELLS = 1 << 15;
 constexpr int ROOT_CHUNK = 1024;                 // root candidates per root range frame
 
 // Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
-bool trace_on() {
+// SGE_TRACE: unset or "0" off; "errors" prints only failures; anything else
+// also prints per-launch timings (which adds synchronisation).
+bool trace_errors() {
     static const bool on = std::getenv("SGE_TRACE") != nullptr && std::getenv("SGE_TRACE")[0] != '0';
+    return on;
+}
+bool trace_on() {
+    static const bool on = trace_errors() && std::strcmp(std::getenv("SGE_TRACE"), "errors") != 0;
     return on;
 }
 
@@ -229,11 +235,11 @@ struct Workspace {
     DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag;
     DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
-    DevBuf mbuf, ckpt;
+    DevBuf mbuf, ckpt, wtrace;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void release() {
         for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
-                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt})
+                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt, &wtrace})
             b->release();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -286,6 +292,7 @@ sge_status fail(sge_ctx *ctx, sge_status code, const std::string &msg) {
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->err = msg;
     }
+    if (trace_errors()) std::fprintf(stderr, "[sge] error %d: %s\n", code, msg.c_str());
     return code;
 }
 
@@ -835,29 +842,21 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     if (nfront > 0) {
         CK(W.pool.ensure((size_t)POOL_CELLS * POOL_STRIDE * 4), "alloc pool");
         CK(W.pseq.ensure((size_t)POOL_CELLS * 8), "alloc pool seq");
-        CK(W.ctl.ensure(64 * 8), "alloc control");
-        CK(cudaMemsetAsync(W.ctl.p, 0, 64 * 8, st), "clear control");
+        CK(W.ctl.ensure(CTL_BYTES), "alloc control");
+        CK(cudaMemsetAsync(W.ctl.p, 0, CTL_BYTES, st), "clear control");
         CK(launch_pool_init(W.pseq.as<unsigned long long>(), POOL_CELLS, st), "pool init");
         ++launches;
-        unsigned long long *c64 = W.ctl.as<unsigned long long>();
         SearchCtl C;
         std::memset(&C, 0, sizeof(C));
+        bind_control(C, W.ctl.p);
         C.front = W.front[cur].as<int32_t>();
         C.nfront = nfront;
         C.fstride = fstride;
         C.shard_index = shard_index;
         C.shard_count = shard_count;
         C.pcap = POOL_CELLS;
-        C.fnext = c64 + 0;
         C.pool = W.pool.as<int32_t>();
         C.pseq = W.pseq.as<unsigned long long>();
-        C.phead = c64 + 1;
-        C.ptail = c64 + 2;
-        C.donations = c64 + 3;
-        int *c32 = reinterpret_cast<int *>(c64 + 8);
-        C.outstanding = c32 + 0;
-        C.idle = c32 + 1;
-        C.status = c32 + 2;
         const int nf32 = (int)nfront;
         CK(cudaMemcpyAsync(C.outstanding, &nf32, sizeof(int), cudaMemcpyHostToDevice, st), "init outstanding");
         C.cancel = ctx->cancel_dev;
@@ -865,11 +864,13 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         C.budget = o.state_budget;
         C.donate = o.no_donation ? 0 : 1;
         C.gran = o.steal_granularity > 0 ? o.steal_granularity : 2;
-        // donation cadence: the CSR kernel's deep, narrow searches need it often; the
-        // bitset kernel's short expansions lose more to donation churn than they gain
+        // donation cadence: a busy warp checks whether idle warps wait for work at most once
+        // per this many iterations or this much device time.  Donating costs a few microseconds
+        // (two fetch-and-adds and one cell write), so the bitset kernel checks every 50 us; the
+        // CSR kernel's searches are mostly finished by the breadth-first split and keep 500 us.
         const bool bits_k = kernel == SGE_KERNEL_BITSET;
         C.donate_iters = o.donate_every_iters > 0 ? o.donate_every_iters : (bits_k ? (1 << 30) : 1024);
-        C.donate_ns = (unsigned long long)(o.donate_every_us > 0 ? o.donate_every_us : (bits_k ? 2000 : 500)) * 1000ull;
+        C.donate_ns = (unsigned long long)(o.donate_every_us > 0 ? o.donate_every_us : (bits_k ? 50 : 500)) * 1000ull;
         // serving groups: idle warps leave after 20 us so a group's tail frees block slots
         // for the next group's kernels
         C.idle_exit_ns = serving ? 20000ull : 0ull;
@@ -897,6 +898,12 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             C.ckpt_n = reinterpret_cast<unsigned long long *>(W.ckpt.as<char>() + bytes);
             CK(cudaMemsetAsync(C.ckpt_n, 0, 8, st), "clear checkpoint");
         }
+        if (trace_on()) {
+            CK(W.wtrace.ensure((size_t)max_grid * search_warps_per_block() * WTRACE_WORDS * 8), "alloc warp trace");
+            CK(cudaMemsetAsync(W.wtrace.p, 0, (size_t)max_grid * search_warps_per_block() * WTRACE_WORDS * 8, st),
+               "clear warp trace");
+            C.wtrace = W.wtrace.as<unsigned long long>();
+        }
         CK(cudaEventRecord(W.ev0, st), "event record");
         CK(launch_search(kfam, W.jobs.as<JobDesc>(), C, kmax, nwl, directed ? 1 : 0, o.blocks_per_sm, max_grid, &grid,
                          st), "search launch");
@@ -908,14 +915,72 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         CK(cudaStreamSynchronize(st), "search sync");
         CK(cudaEventElapsedTime(&kernel_ms, W.ev0, W.ev1), "event time");
         donations = (long long)dn;
-        if (trace_on())
+        if (trace_on()) {
             std::fprintf(stderr, "[sge] search grid %d frames %lld kernel %.3f ms status %d donations %llu\n", grid,
                          nfront, kernel_ms, status, dn);
+            // warp timeline: when warps exit relative to the first start, and their busy share
+            const size_t nw = (size_t)grid * search_warps_per_block();
+            constexpr int TW = WTRACE_WORDS;   // words per warp record
+            std::vector<unsigned long long> wt(nw * TW);
+            CK(cudaMemcpy(wt.data(), W.wtrace.p, nw * TW * 8, cudaMemcpyDeviceToHost), "read warp trace");
+            unsigned long long t0 = ~0ull;
+            for (size_t w = 0; w < nw; ++w)
+                if (wt[TW * w]) t0 = std::min(t0, wt[TW * w]);
+            std::vector<double> ex, last;
+            std::vector<size_t> order;
+            double busy = 0, span = 0;
+            for (size_t w = 0; w < nw; ++w) {
+                if (!wt[TW * w]) continue;
+                ex.push_back((wt[TW * w + 1] - t0) * 1e-6);
+                last.push_back(wt[TW * w + 3] ? (wt[TW * w + 3] - t0) * 1e-6 : 0.0);
+                busy += wt[TW * w + 2] * 1e-6;
+                span = std::max(span, ex.back());
+                order.push_back(w);
+            }
+            std::sort(ex.begin(), ex.end());
+            std::sort(last.begin(), last.end());
+            auto q = [](const std::vector<double> &v, double f) {
+                return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(f * v.size()))];
+            };
+            std::fprintf(stderr,
+                         "[sge] warps %zu: exit at p50 %.3f max %.3f ms; last work at p10 %.3f p50 %.3f p90 %.3f "
+                         "p99 %.3f ms; busy %.1f%% of warps x span\n",
+                         ex.size(), q(ex, 0.5), span, q(last, 0.1), q(last, 0.5), q(last, 0.9), q(last, 0.99),
+                         span > 0 ? 100.0 * busy / (span * ex.size()) : 0.0);
+            double don_ms = 0, don_ev = 0, don_fr = 0, don_max = 0;
+            for (size_t w : order) {
+                don_ms += wt[TW * w + 9] * 1e-6;
+                don_ev += (double)wt[TW * w + 10];
+                don_fr += (double)wt[TW * w + 11];
+                don_max = std::max(don_max, wt[TW * w + 9] * 1e-6);
+            }
+            {
+                double qn = 0, qt = 0, qs = 0;
+                for (size_t w : order) {
+                    qn += (double)wt[TW * w + 12];
+                    qt += wt[TW * w + 13] * 1e-6;
+                    qs += (double)wt[TW * w + 14];
+                }
+                std::fprintf(stderr, "[sge] queue frames %.0f: %.1f warp-ms, %.3g states\n", qn, qt, qs);
+            }
+            std::fprintf(stderr, "[sge] donation: %.0f events, %.0f frames, %.3f warp-ms in total, %.3f ms at most in "
+                         "one warp, %.2f us per event\n", don_ev, don_fr, don_ms, don_max,
+                         don_ev > 0 ? 1000.0 * don_ms / don_ev : 0.0);
+            std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return wt[TW * a + 4] > wt[TW * b + 4]; });
+            for (size_t r = 0; r < std::min<size_t>(8, order.size()); ++r) {
+                const unsigned long long *x = &wt[TW * order[r]];
+                std::fprintf(stderr,
+                             "[sge]   longest frame %zu: %.3f ms, ended at %.3f ms, job %llu depth %llu from %s, "
+                             "states %llu nodes %llu\n",
+                             r, x[4] * 1e-6, (x[3] - t0) * 1e-6, x[5] & 0xffff, (x[5] >> 16) & 0x3fff,
+                             (x[5] >> 30) == 1 ? "frontier" : "queue", x[6], x[7]);
+            }
+        }
         if (ckpt_frames != nullptr && (status == SGE_ERR_BUDGET || status == SGE_ERR_TIMEOUT ||
                                        status == SGE_ERR_CANCELLED)) {
             // unexplored work = the warps' dumps + frontier frames never taken + queued frames
-            unsigned long long hc[4] = {0, 0, 0, 0}, nd = 0;
-            CK(cudaMemcpyAsync(hc, c64, sizeof(hc), cudaMemcpyDeviceToHost, st), "read control");
+            unsigned long long hc[1] = {0}, nd = 0;   // fnext
+            CK(cudaMemcpyAsync(&hc[0], C.fnext, 8, cudaMemcpyDeviceToHost, st), "read control");
             CK(cudaMemcpyAsync(&nd, C.ckpt_n, 8, cudaMemcpyDeviceToHost, st), "read checkpoint count");
             CK(cudaStreamSynchronize(st), "checkpoint sync");
             if ((long long)nd > C.ckpt_cap) return fail(ctx, SGE_ERR_OOM, "checkpoint larger than its buffer");
@@ -934,12 +999,14 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             const long long taken = std::min<long long>((long long)hc[0], nfront);
             CK(take(C.front + (taken * shard_count + shard_index) * (long long)fstride, nfront - taken, fstride,
                     (long long)fstride * shard_count), "read frontier");
-            // queued frames never taken: cells [head, tail) of the ring
-            for (unsigned long long t = hc[1]; t < hc[2];) {
-                const unsigned long long cell = t % POOL_CELLS;
-                const unsigned long long n = std::min<unsigned long long>(hc[2] - t, POOL_CELLS - cell);
-                CK(take(C.pool + (size_t)cell * POOL_STRIDE, (long long)n, POOL_STRIDE, POOL_STRIDE), "read queue");
-                t += n;
+            // queued frames never taken: the cells left published (sequence word = ticket + 1)
+            std::vector<unsigned long long> seq(POOL_CELLS);
+            CK(cudaMemcpyAsync(seq.data(), C.pseq, (size_t)POOL_CELLS * 8, cudaMemcpyDeviceToHost, st), "read queue");
+            CK(cudaStreamSynchronize(st), "checkpoint sync");
+            for (int cell = 0; cell < POOL_CELLS; ++cell) {
+                const unsigned long long sv = seq[cell];
+                if (sv >= 1 && (sv >> 63) == 0 && (sv - 1) % POOL_CELLS == (unsigned long long)cell)
+                    CK(take(C.pool + (size_t)cell * POOL_STRIDE, 1, POOL_STRIDE, POOL_STRIDE), "read queue");
             }
             CK(cudaStreamSynchronize(st), "checkpoint sync");
             if (ckpt_kmax) *ckpt_kmax = kmax;
@@ -1640,7 +1707,7 @@ sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
     };
     JobDesc *djob = reinterpret_cast<JobDesc *>(take(sizeof(JobDesc)));
     unsigned long long *dctr = reinterpret_cast<unsigned long long *>(take(6 * 8));
-    unsigned long long *dctl = reinterpret_cast<unsigned long long *>(take(64 * 8));
+    unsigned char *dctl = take(CTL_BYTES);
     int32_t *dfront = reinterpret_cast<int32_t *>(take(FRAME_HDR * 4));
     PosInfo *dpos = reinterpret_cast<PosInfo *>(take((size_t)k * sizeof(PosInfo)));
     BackEdge *dback = reinterpret_cast<BackEdge *>(take((size_t)(nb > 0 ? nb : 1) * sizeof(BackEdge)));
@@ -1667,38 +1734,31 @@ sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
     D.abytes = dctr + 5;
     const int32_t root[FRAME_HDR] = {0, 0, -1, -1};
     const int one = 1;
-    int *c32 = reinterpret_cast<int *>(dctl + 8);
+    SearchCtl C;
+    std::memset(&C, 0, sizeof(C));
+    bind_control(C, dctl);
     cudaError_t e = cudaSuccess;
     auto ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     ok(launch_make_vld(d_rowptr, d_vlabel, dvld, n, st));
     if (zero_elab) ok(cudaMemsetAsync(delab, 0, (size_t)nnz * 4, st));
     // every call shares the array: clear what must start at zero
     ok(cudaMemsetAsync(dctr, 0, 6 * 8, st));
-    ok(cudaMemsetAsync(dctl, 0, 64 * 8, st));
+    ok(cudaMemsetAsync(dctl, 0, CTL_BYTES, st));
     ok(cudaMemcpyAsync(djob, &D, sizeof(D), cudaMemcpyHostToDevice, st));
     ok(cudaMemcpyAsync(dpos, pos, (size_t)k * sizeof(PosInfo), cudaMemcpyHostToDevice, st));
     if (nb > 0) ok(cudaMemcpyAsync(dback, back, (size_t)nb * sizeof(BackEdge), cudaMemcpyHostToDevice, st));
     ok(cudaMemcpyAsync(dfront, root, sizeof(root), cudaMemcpyHostToDevice, st));
-    ok(cudaMemcpyAsync(c32, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    ok(cudaMemcpyAsync(C.outstanding, &one, sizeof(int), cudaMemcpyHostToDevice, st));
     ok(launch_pool_init(dseq, POOL, st));
     if (e != cudaSuccess) return SGE_ERR_CUDA;
-    SearchCtl C;
-    std::memset(&C, 0, sizeof(C));
     C.front = dfront;
     C.nfront = 1;
     C.fstride = FRAME_HDR;
     C.shard_index = 0;
     C.shard_count = 1;
     C.pcap = POOL;
-    C.fnext = dctl + 0;
     C.pool = dpool;
     C.pseq = dseq;
-    C.phead = dctl + 1;
-    C.ptail = dctl + 2;
-    C.donations = dctl + 3;
-    C.outstanding = c32 + 0;
-    C.idle = c32 + 1;
-    C.status = c32 + 2;
     if (time_limit_ms <= 0) {
         const char *env = std::getenv("SGE_TIME_LIMIT_MS");
         if (env) time_limit_ms = std::atoll(env);

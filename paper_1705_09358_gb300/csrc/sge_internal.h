@@ -124,6 +124,7 @@ struct SearchCtl {
     int *idle;                  // warps waiting for work
     int *status;                // first error code (0 = ok)
     unsigned long long *donations;
+    int *promised;              // donations decided on but not yet pushed (bounds concurrent donors)
     const volatile int *cancel; // host-mapped cancel word (nonzero = stop), or null
     unsigned long long deadline_ns;  // time limit in ns from each warp's start (%globaltimer), 0 = none
     long long budget;           // states budget per job, 0 = none
@@ -137,7 +138,28 @@ struct SearchCtl {
     long long ckpt_cap;         // ... up to this many frames of ckpt_stride ints
     int32_t ckpt_stride;        // FRAME_HDR + kmax
     unsigned long long *ckpt_n; // frames dumped (may exceed ckpt_cap: then the dump is incomplete)
+    unsigned long long *wtrace; // optional per-warp trace records of WTRACE_WORDS words (null: off)
 };
+
+constexpr int WTRACE_WORDS = 16;   // words of one warp's trace record (see WarpClock)
+
+// The control words of a search launch live in a block of CTL_BYTES bytes,
+// each on its own 128-byte line: idle warps poll some of them while busy
+// warps update others with atomics, and sharing one line would queue every
+// update behind the polls.
+constexpr size_t CTL_LINE = 128;
+constexpr size_t CTL_BYTES = 8 * CTL_LINE;
+inline void bind_control(SearchCtl &C, void *block) {
+    char *b = static_cast<char *>(block);
+    C.fnext = reinterpret_cast<unsigned long long *>(b + 0 * CTL_LINE);
+    C.phead = reinterpret_cast<unsigned long long *>(b + 1 * CTL_LINE);
+    C.ptail = reinterpret_cast<unsigned long long *>(b + 2 * CTL_LINE);
+    C.donations = reinterpret_cast<unsigned long long *>(b + 3 * CTL_LINE);
+    C.outstanding = reinterpret_cast<int *>(b + 4 * CTL_LINE);
+    C.idle = reinterpret_cast<int *>(b + 5 * CTL_LINE);
+    C.status = reinterpret_cast<int *>(b + 6 * CTL_LINE);
+    C.promised = reinterpret_cast<int *>(b + 7 * CTL_LINE);
+}
 
 // ------------------------------------------------------------ launchers
 // (implemented in sge_kernels.cu; all launch on `st`)

@@ -36,8 +36,14 @@ constexpr unsigned long long CHECK_NS = 20000;         // device time between do
 // whose iterations are an order of magnitude cheaper)
 constexpr unsigned long long CANCEL_CHECK_NS = 1000000; // device time between reads of the host cancel word
 constexpr int DONATE_MIN_LEVELS = 2;     // a donated node keeps at least this many levels below it
-constexpr long long IDLE_SPIN_LIMIT = 1ll << 31;
-constexpr int QUEUE_ATTEMPTS = 64;
+constexpr unsigned long long IDLE_GUARD_NS = 60ull * 1000000000ull;   // 60 s idle: internal error
+constexpr long long RESERVE_SPIN_LIMIT = 1 << 20;   // bounded wait for a queue cell's previous lap
+constexpr int RESERVE_TICKETS = 64;                  // producer tickets tried before keeping the work
+// Idle back-off caps (ns): one warp per block polls for work at short
+// intervals, the others at long ones, so thousands of idle warps do not
+// crowd the queue's lines while the busy warps use them.
+constexpr unsigned IDLE_BACKOFF_FAST = 1024;
+constexpr unsigned IDLE_BACKOFF_SLOW = 32768;
 
 __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -62,17 +68,21 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-__device__ __forceinline__ unsigned long long load_acquire(unsigned long long *p) {
-    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
-    return r.load(cuda::memory_order_acquire);
+// Strong (gpu-scope) loads and stores of the words warps poll and publish:
+// they are ordered and always see the latest value at the point of coherence
+// (L2), never a copy left in a streaming multiprocessor's L1.
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 __device__ __forceinline__ void store_release(unsigned long long *p, unsigned long long v) {
-    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*p);
-    r.store(v, cuda::memory_order_release);
+    asm volatile("st.release.gpu.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ int load_relaxed(int *p) {
-    cuda::atomic_ref<int, cuda::thread_scope_device> r(*p);
-    return r.load(cuda::memory_order_relaxed);
+__device__ __forceinline__ int load_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
@@ -694,42 +704,69 @@ __global__ void __launch_bounds__(BLOCK) k_scan_add(long long *out, long long n,
 
 // ========================================================= frame queue
 
-// Bounded multi-producer multi-consumer queue with per-cell sequence numbers
-// (cell c starts at seq c; a producer owns ticket t when seq == t, a consumer
-// when seq == t + 1).  Lane 0 only.  Neither call waits: each returns -1 when
-// the queue is full / empty or after QUEUE_ATTEMPTS contended tries.
+// Ticket queue of donated frames.  Producers (donating warps) and consumers
+// (idle warps) each draw tickets from their own counter with one
+// fetch-and-add; ticket t of either side meets at cell t mod cap, whose
+// sequence word walks through
+//     t  (free for ticket t)  ->  t | CELL_LOCK  (producer t writing)
+//        ->  t + 1  (published)  ->  t + cap  (consumed: free for t + cap)
+// or, if consumer t leaves before producer t arrives,  t -> t + cap
+// (abandoned; producer t then draws another ticket).  A consumer waits on
+// its own cell only, so no line is fought over however many warps are idle,
+// and every frame reaches exactly one consumer.  Lane 0 only.
+constexpr unsigned long long CELL_LOCK = 1ull << 63;
+
+// Producer: a ticket whose cell is locked for writing, or -1 (the caller keeps its work).
 __device__ long long queue_reserve(const SearchCtl &C) {
-    unsigned long long pos = load_acquire(C.ptail);
-    for (int a = 0; a < QUEUE_ATTEMPTS; ++a) {
-        const unsigned long long seq = load_acquire(C.pseq + (pos % (unsigned long long)C.pcap));
-        const long long dif = (long long)(seq - pos);
-        if (dif == 0) {
-            if (atomicCAS(C.ptail, pos, pos + 1) == pos) return (long long)pos;
-            pos = load_acquire(C.ptail);
-        } else if (dif < 0) {
-            return -1;
-        } else {
-            pos = load_acquire(C.ptail);
+    const unsigned long long cap = (unsigned long long)C.pcap;
+    for (int a = 0; a < RESERVE_TICKETS; ++a) {
+        const unsigned long long t = atomicAdd(C.ptail, 1ull);
+        unsigned long long *seq = C.pseq + t % cap;
+        for (long long spin = 0;; ++spin) {
+            const unsigned long long sv = load_acquire(seq);
+            if (sv == t) {
+                if (atomicCAS(seq, t, t | CELL_LOCK) == t) return (long long)t;
+                continue;                                   // consumer t left meanwhile: look again
+            }
+            if ((sv & ~CELL_LOCK) > t) break;               // consumer t left: draw another ticket
+            if (spin > RESERVE_SPIN_LIMIT) {                // the cell's previous lap never ended
+                set_status(C.status, -3);
+                return -1;
+            }
+            __nanosleep(128);
         }
     }
     return -1;
 }
 
-__device__ long long queue_claim(const SearchCtl &C) {
-    unsigned long long pos = load_acquire(C.phead);
-    for (int a = 0; a < QUEUE_ATTEMPTS; ++a) {
-        const unsigned long long seq = load_acquire(C.pseq + (pos % (unsigned long long)C.pcap));
-        const long long dif = (long long)(seq - (pos + 1));
-        if (dif == 0) {
-            if (atomicCAS(C.phead, pos, pos + 1) == pos) return (long long)pos;
-            pos = load_acquire(C.phead);
-        } else if (dif < 0) {
-            return -1;
-        } else {
-            pos = load_acquire(C.phead);
+// Consumer holding ticket t: is its frame published?
+__device__ __forceinline__ bool queue_ready(const SearchCtl &C, unsigned long long t) {
+    return load_acquire(C.pseq + t % (unsigned long long)C.pcap) == t + 1;
+}
+
+// Consumer holding ticket t wants to leave: true if it left (no frame will
+// come to it), false if its frame is published (the caller takes it) or, when
+// not stopping, if the cell is still in its previous lap (the caller stays).
+// A stopping consumer leaves a cell in its previous lap as it is: a frame
+// published there later is found among the unconsumed cells after the launch.
+__device__ bool queue_leave(const SearchCtl &C, unsigned long long t, bool stopping) {
+    const unsigned long long cap = (unsigned long long)C.pcap;
+    unsigned long long *seq = C.pseq + t % cap;
+    for (long long spin = 0;; ++spin) {
+        const unsigned long long sv = load_acquire(seq);
+        if (sv == t + 1) return false;
+        if (sv == t) {
+            if (atomicCAS(seq, t, t + cap) == t) return true;
+            continue;
         }
+        if (!(sv & CELL_LOCK) && sv < t) return stopping;   // previous lap still in use
+        // locked by producer t, which publishes within a few instructions: wait
+        if (spin > RESERVE_SPIN_LIMIT) {
+            set_status(C.status, -3);
+            return true;
+        }
+        __nanosleep(128);
     }
-    return -1;
 }
 
 // Warp-collective: push frame [j, depth, beg, end, M[0..mlen-1] (+ last)]
@@ -751,7 +788,7 @@ __device__ bool push_frame(const SearchCtl &C, int j, int depth, int beg, int en
     __syncwarp();
     if (lane == 0) {
         __threadfence();
-        store_release(C.pseq + (t % C.pcap), (unsigned long long)t + 1);
+        store_release(C.pseq + (t % C.pcap), (unsigned long long)t + 1);   // publish (clears the lock)
         atomicAdd(C.donations, 1ull);
     }
     __syncwarp();
@@ -762,6 +799,58 @@ struct Frame {
     int job, depth, beg, end;
     bool counted;   // FRAME_COUNTED: the range's accepted nodes and states are already counted
 };
+
+// Optional per-warp timing, kept in the warp's own trace record (no registers):
+// {start, exit, busy, last frame end, longest frame's duration, its
+// job | depth << 16 | origin << 30 (1 frontier, 2 queue), its states, its
+// nodes, origin of the current frame, ns spent donating, donation events,
+// frames donated, frames taken from the queue, ns and states in them, 0}
+// (WTRACE_WORDS words).
+struct WarpClock {
+    __device__ static unsigned long long *rec(const SearchCtl &C) {
+        return C.wtrace + WTRACE_WORDS * ((size_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5));
+    }
+    __device__ static void begin(const SearchCtl &C) {
+        if (C.wtrace && (threadIdx.x & 31) == 0) rec(C)[0] = globaltimer();
+    }
+    __device__ static void origin(const SearchCtl &C, int kind) {
+        if (C.wtrace && (threadIdx.x & 31) == 0) rec(C)[8] = (unsigned long long)kind;
+    }
+    __device__ static void frame_in(const SearchCtl &C) {
+        if (C.wtrace && (threadIdx.x & 31) == 0) rec(C)[3] = globaltimer();
+    }
+    __device__ static void frame_out(const SearchCtl &C, const Frame &fr, unsigned long long st,
+                                     unsigned long long nd) {
+        if (C.wtrace && (threadIdx.x & 31) == 0) {
+            unsigned long long *w = rec(C);
+            const unsigned long long now = globaltimer(), dur = now - w[3];
+            w[2] += dur;
+            w[3] = now;   // after the last frame: when the warp last held work
+            if (w[8] == 2) { w[12] += 1; w[13] += dur; w[14] += st; }
+            if (dur > w[4]) {
+                w[4] = dur;
+                w[5] = (unsigned long long)fr.job | ((unsigned long long)fr.depth << 16) | (w[8] << 30);
+                w[6] = st;
+                w[7] = nd;
+            }
+        }
+    }
+    __device__ static void finish(const SearchCtl &C) {
+        if (C.wtrace && (threadIdx.x & 31) == 0) rec(C)[1] = globaltimer();
+    }
+    __device__ static unsigned long long don_begin(const SearchCtl &C) {
+        return (C.wtrace && (threadIdx.x & 31) == 0) ? globaltimer() : 0ull;
+    }
+    __device__ static void don_end(const SearchCtl &C, unsigned long long t, int given) {
+        if (C.wtrace && (threadIdx.x & 31) == 0) {
+            unsigned long long *w = rec(C);
+            w[9] += globaltimer() - t;
+            w[10] += 1;
+            w[11] += (unsigned long long)given;
+        }
+    }
+};
+
 
 // Warp-collective: append range frame [j, depth (| FRAME_COUNTED), beg, end,
 // M[0..depth-1]] to the checkpoint.  Every warp dumps at most two frames per
@@ -802,43 +891,55 @@ __device__ bool acquire_frame(const SearchCtl &C, int *M, Frame &fr, unsigned lo
     unsigned long long idle_since = 0;
     int kind = 0;        // 1 frontier, 2 queue, 0 stop
     long long idx = -1;
+    long long ticket = -1;   // consumer ticket held (lane 0)
     for (;;) {
         kind = -1;
         if (lane == 0) {
             if (load_relaxed(C.status) != 0) {
-                kind = 0;
+                // stopping: leave the ticket, or take the frame already sent to it
+                if (ticket >= 0 && !queue_leave(C, (unsigned long long)ticket, true)) { kind = 2; idx = ticket; }
+                else kind = 0;
             } else {
-                if (load_acquire(C.fnext) < (unsigned long long)C.nfront) {
+                if (ticket < 0 && load_acquire(C.fnext) < (unsigned long long)C.nfront) {
                     const unsigned long long f = atomicAdd(C.fnext, 1ull);
                     if ((long long)f < C.nfront) { kind = 1; idx = (long long)f; }
                 }
                 if (kind < 0) {
-                    const long long t = queue_claim(C);
-                    if (t >= 0) { kind = 2; idx = t; }
+                    if (ticket < 0) ticket = (long long)atomicAdd(C.phead, 1ull);
+                    if (queue_ready(C, (unsigned long long)ticket)) { kind = 2; idx = ticket; }
                 }
+                // all work done: no frame can come to the ticket any more
                 if (kind < 0 && load_relaxed(C.outstanding) == 0) kind = 0;
             }
             if (kind < 0) {
                 if (!idle) { atomicAdd(C.idle, 1); idle = true; idle_since = globaltimer(); }
-                // optional early exit of a warp that found no work for a while: the warps that
-                // still hold frames finish every queued frame themselves, so no frame is lost,
-                // and the freed block slots serve kernels launched on other streams
-                else if (C.idle_exit_ns != 0 && globaltimer() - idle_since > C.idle_exit_ns) kind = 0;
-                if (++spins > IDLE_SPIN_LIMIT) { set_status(C.status, -5); kind = 0; }
-                else if ((spins & 1023) == 0) {
-                    if ((C.cancel != nullptr && *C.cancel != 0)) { set_status(C.status, -6); kind = 0; }
-                    else if (deadline != 0 && globaltimer() > deadline) { set_status(C.status, -5); kind = 0; }
+                // optional early exit of a warp that found no work for a while (it leaves its
+                // ticket first; a frame already sent to it is taken instead), so the freed block
+                // slots serve kernels launched on other streams
+                else if (C.idle_exit_ns != 0 && globaltimer() - idle_since > C.idle_exit_ns) {
+                    if (queue_leave(C, (unsigned long long)ticket, false)) kind = 0;
+                    else if (queue_ready(C, (unsigned long long)ticket)) { kind = 2; idx = ticket; }
+                    else idle_since = globaltimer();   // previous lap still in use: stay a while
+                }
+                if (kind < 0 && (++spins & 1023) == 0) {
+                    // the stop paths set the status; the next round leaves the ticket.  A warp idle
+                    // far longer than any search leaves a frame to wait ends the launch with an error.
+                    const unsigned long long now = globaltimer();
+                    if ((C.cancel != nullptr && *C.cancel != 0)) set_status(C.status, -6);
+                    else if (deadline != 0 && now > deadline) set_status(C.status, -5);
+                    else if (now - idle_since > IDLE_GUARD_NS) set_status(C.status, -3);
                 }
             }
         }
         kind = __shfl_sync(FULL, kind, 0);
         if (kind >= 0) break;
-        // exponential backoff keeps idle warps from crowding the queue's cache lines
+        // exponential backoff: one warp per block polls often, the others rarely
         __nanosleep(backoff);
-        if (backoff < 8192) backoff <<= 1;
+        if (backoff < ((threadIdx.x >> 5) == 0 ? IDLE_BACKOFF_FAST : IDLE_BACKOFF_SLOW)) backoff <<= 1;
     }
     if (lane == 0 && idle) atomicSub(C.idle, 1);
     if (kind == 0) return false;
+    WarpClock::origin(C, kind);
     idx = __shfl_sync(FULL, idx, 0);
     const int32_t *src;
     if (kind == 1) {
@@ -890,16 +991,24 @@ __device__ __forceinline__ bool time_to_check(unsigned long long &last) {
     return true;
 }
 
-__device__ __forceinline__ bool donation_wanted(const SearchCtl &C) {
-    int want = 0;
+// Warp-uniform: should this warp donate now?  Donation is wanted while more
+// warps are idle than frames wait in the queue; a donor first takes one of
+// those (idle - queued) slots, so a few donors, not every busy warp, answer
+// one idle warp.  A true result must be paired with donation_done().
+__device__ __forceinline__ bool donation_claim(const SearchCtl &C) {
+    int ok = 0;
     if ((threadIdx.x & 31) == 0 && C.donate) {
-        const int idle = load_relaxed(C.idle);
-        if (idle > 0) {
-            const long long occ = (long long)(load_acquire(C.ptail) - load_acquire(C.phead));
-            want = occ < idle && occ < C.pcap / 2;
-        }
+        // consumer tickets not yet matched by a producer = idle warps waiting for a frame
+        const long long waiting = (long long)(load_acquire(C.phead) - load_acquire(C.ptail));
+        if (waiting > 0 && atomicAdd(C.promised, 1) < waiting) ok = 1;
+        else if (waiting > 0) atomicSub(C.promised, 1);
     }
-    return __shfl_sync(FULL, want, 0) != 0;
+    return __shfl_sync(FULL, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void donation_done(const SearchCtl &C) {
+    if ((threadIdx.x & 31) == 0) atomicSub(C.promised, 1);
+    __syncwarp();
 }
 
 // ===================================================== search: CSR kernel
@@ -999,7 +1108,9 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
     unsigned long long last_check = 0, last_don_ns = 0, last_cancel = 0;
     int cur_job = -1;
     CsrJob B;
+    WarpClock::begin(C);
     while (acquire_frame(C, M, fr, deadline)) {
+        WarpClock::frame_in(C);
         const JobDesc &J = jobs[fr.job];
         if (fr.job != cur_job) {
             cur_job = fr.job;
@@ -1059,7 +1170,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                 }
                 if (must_stop(C, J, st, deadline, last_check, last_cancel)) { stopped = true; break; }
                 if ((iter - last_don_iter >= C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
-                    donation_wanted(C)) {
+                    donation_claim(C)) {
                     // donate the shallowest unexplored work: half of an unscanned
                     // range, else up to `gran` pending survivors as new search nodes
                     last_don_iter = iter;
@@ -1093,6 +1204,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                             break;
                         }
                     }
+                    donation_done(C);
                 }
             }
             LvCsr &L = lv[lvl];
@@ -1172,8 +1284,10 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             if (!stopped) atomicSub(C.outstanding, 1);
         }
         __syncwarp();
+        WarpClock::frame_out(C, fr, st, nd);
         if (stopped) break;
     }
+    WarpClock::finish(C);
 }
 
 // ================================================== search: bitset kernel
@@ -1199,6 +1313,7 @@ struct PosB {
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
     return round16((size_t)nwl * 32 * 8 +                   // used bitset
+                   8 +                                      // the frame's range (for checkpoints)
                    (size_t)kmax * 4 +                       // M
                    (size_t)kmax * sizeof(PosB) +            // position table
                    (size_t)kmax * LIST_CAP * 2 +            // survivor lists
@@ -1223,6 +1338,7 @@ struct BitsWarp {
     uint16_t *lst;     // [kmax][LIST_CAP]
     uint8_t *lcnt;     // [kmax]
     uint8_t *tback;
+    int *frange;       // [2]: the current frame's candidate range
     uint64_t *slab;    // global: [kmax][NWL * 32]
 };
 
@@ -1399,7 +1515,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
     BitsWarp W;
     W.used = reinterpret_cast<uint64_t *>(base);
-    W.M = reinterpret_cast<int *>(W.used + NWL * 32);
+    W.frange = reinterpret_cast<int *>(W.used + NWL * 32);
+    W.M = W.frange + 2;
     W.tab = reinterpret_cast<PosB *>(W.M + kmax);
     W.lst = reinterpret_cast<uint16_t *>(W.tab + kmax);
     W.lcnt = reinterpret_cast<uint8_t *>(W.lst + (size_t)kmax * LIST_CAP);
@@ -1413,7 +1530,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     unsigned long long last_check = 0, last_don_ns = 0, last_cancel = 0;
     int cur_job = -1;
     BitsJob B;
+    WarpClock::begin(C);
     while (acquire_frame(C, M, fr, deadline)) {
+        WarpClock::frame_in(C);
         const JobDesc &J = jobs[fr.job];
         if (fr.job != cur_job) {
             // cache the job's pointers in registers and its position table in shared memory
@@ -1466,6 +1585,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             else if (lst) { vlo = __ldg(lst + b0 + fr.beg); vhi = __ldg(lst + b0 + e - 1); }
             else { vlo = fr.beg; vhi = e - 1; }
         }
+        if (lane == 0) { W.frange[0] = fr.beg; W.frange[1] = fr.end; }   // read back only by a checkpoint
         const bool count_len = fr.beg <= 0 && !fr.counted;
         const bool leaf0 = d0 == k - 1;
         const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, d0, leaf0, st, hs, ab, vlo, vhi, count_len)
@@ -1483,12 +1603,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     }
                     if (must_stop(C, J, st, deadline, last_check, last_cancel)) { stopped = true; break; }
                     if ((iter - last_don_iter >= C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
-                        donation_wanted(C)) {
+                        donation_claim(C)) {
                         // donate up to `gran` pending survivors of the shallowest level that has some
                         last_don_iter = iter;
                         last_don_ns = last_check;
+                        const unsigned long long tdon = WarpClock::don_begin(C);
+                        int given = 0;
                         for (int l = d0; l <= lvl && l + 1 + DONATE_MIN_LEVELS <= k; ++l) {
-                            int given = 0;
+                            given = 0;
                             while (given < C.gran) {
                                 const int v = bits_next<NWL>(W, l);
                                 if (v < 0) break;
@@ -1501,6 +1623,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                             }
                             if (given > 0) break;
                         }
+                        WarpClock::don_end(C, tdon, given);
+                        donation_done(C);
                     }
                 }
                 const int prev = M[lvl];
@@ -1545,7 +1669,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         len = J.pos[l].ucnt;
                     }
                     int lo = 0, hi = len;   // the level's own range
-                    if (l == d0 && fr.beg >= 0) { lo = fr.beg; hi = min(fr.end, len); }
+                    if (l == d0 && W.frange[0] >= 0) { lo = W.frange[0]; hi = min(W.frange[1], len); }
                     const int c = W.lcnt[l];
                     if (c == 0) continue;
                     if (c != LIST_SPILLED) {
@@ -1570,8 +1694,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             if (!stopped) atomicSub(C.outstanding, 1);
         }
         __syncwarp();
+        WarpClock::frame_out(C, fr, st, nd);
         if (stopped) break;
     }
+    WarpClock::finish(C);
 }
 
 unsigned grid_for(long long warps) {
