@@ -69,8 +69,9 @@ enum {
 typedef struct {
     int32_t algo;              /* SGE_RI .. SGE_RIDS_SI_FC (default SGE_RI) */
     int32_t split_depth;       /* depth of the breadth-first split; 0 = auto */
-    int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 32) */
-    int32_t steal_granularity; /* most frames one donation hands out (default 2) */
+    int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 8) */
+    int32_t steal_granularity; /* most frames one donation hands out (default 16 for the bitset
+                                  kernel, 2 for the CSR kernel) */
     int64_t state_budget;      /* stop after about this many states of one pair (0 = none) */
     int64_t time_limit_ms;     /* stop after about this much search-kernel time (0 = none);
                                   with either limit set the split stops at the frame
@@ -83,7 +84,7 @@ typedef struct {
     int32_t no_donation;       /* 1 = persistent kernel without work donation */
     int32_t donate_every_iters;/* a warp donates at most once per this many search iterations ... */
     int32_t donate_every_us;   /* ... or once per this many microseconds, whichever comes first
-                                  (defaults: CSR kernel 1024 / 500, bitset kernel 2^30 / 2000) */
+                                  (defaults: CSR kernel 1024 / 500, bitset kernel 2^30 / 50) */
     int32_t reserved[3];
 } sge_opts;
 

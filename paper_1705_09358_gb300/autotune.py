@@ -16,9 +16,9 @@ import os
 import time
 
 SPACE = {
-    "frames_per_warp": [8, 16, 32, 64, 128],
-    "steal_granularity": [1, 2, 4, 8],
-    "donate_every_us": [200, 500, 2000, 8000],
+    "frames_per_warp": [4, 8, 16, 32, 64],
+    "steal_granularity": [1, 2, 4, 8, 16, 32],
+    "donate_every_us": [20, 50, 100, 200, 500],
 }
 DEFAULT_PATH = os.path.join(os.path.expanduser("~"), ".cache", "sge_autotune.json")
 

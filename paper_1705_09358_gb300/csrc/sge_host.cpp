@@ -715,7 +715,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     CK(search_blocks_per_sm(kernel == SGE_KERNEL_BITSET ? 2 : 1, kmax, nwl, directed ? 1 : 0, &occ), "occupancy");
     if (o.blocks_per_sm > 0 && o.blocks_per_sm < occ) occ = o.blocks_per_sm;
     const long long resident_warps = (long long)ctx->sms * occ * search_warps_per_block();
-    const long long fpw = o.frames_per_warp > 0 ? o.frames_per_warp : 32;
+    const long long fpw = o.frames_per_warp > 0 ? o.frames_per_warp : 8;
     const long long target_frames = fpw * resident_warps * shard_count;
     // roots: one frame per active job, cut into ranges of ROOT_CHUNK candidates
     // when the root has more (a range frame counts the node's states only if it
@@ -863,7 +863,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         C.deadline_ns = o.time_limit_ms > 0 ? (unsigned long long)o.time_limit_ms * 1000000ull : 0ull;
         C.budget = o.state_budget;
         C.donate = o.no_donation ? 0 : 1;
-        C.gran = o.steal_granularity > 0 ? o.steal_granularity : 2;
+        // a bitset-kernel donor hands out up to 16 of its shallowest pending survivors at once:
+        // with few, large frontier frames the tail is split fastest that way
+        C.gran = o.steal_granularity > 0 ? o.steal_granularity : (kernel == SGE_KERNEL_BITSET ? 16 : 2);
         // donation cadence: a busy warp checks whether idle warps wait for work at most once
         // per this many iterations or this much device time.  Donating costs a few microseconds
         // (two fetch-and-adds and one cell write), so the bitset kernel checks every 50 us; the
