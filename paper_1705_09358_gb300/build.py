@@ -2,7 +2,7 @@
 
     python -m paper_1705_09358_gb300.build [--force]
 
-Three translation units compiled in parallel, then linked with the static CUDA
+Four translation units compiled in parallel, then linked with the static CUDA
 runtime.  Works the same on x86_64 and aarch64 hosts (no host-specific flags).
 """
 from __future__ import annotations
@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsge.so")
 ROOT = os.path.dirname(HERE)
 HEADERS = [os.path.join(ROOT, "include", "sge.h"), os.path.join(CSRC, "sge_internal.h")]
-SOURCES = ["sge_kernels.cu", "sge_host.cpp", "sge_noalloc.cu"]
+SOURCES = ["sge_kernels.cu", "sge_host.cpp", "sge_noalloc.cu", "sge_ingest.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -99,24 +99,36 @@ struct Arc {
 
 // Sort arcs, merge repeats with an equal label; false on a conflicting repeat.
 bool rows_from_arcs(int n, std::vector<Arc> &arcs, Rows &r) {
-    std::sort(arcs.begin(), arcs.end(), [](const Arc &x, const Arc &y) { return x.key < y.key; });
-    size_t w = 0;
-    for (size_t i = 0; i < arcs.size(); ++i) {
-        if (w > 0 && arcs[w - 1].key == arcs[i].key) {
-            if (arcs[w - 1].lab != arcs[i].lab) return false;
+    // two stable counting sorts (by target, then by source) leave every row sorted by
+    // target in O(m + n); repeated arcs end up adjacent and are merged
+    const size_t m = arcs.size();
+    // scratch kept per thread: large temporaries freed after every call cost more in
+    // fresh-page faults than the sorting itself
+    static thread_local std::vector<Arc> tmp;
+    static thread_local std::vector<int64_t> at;
+    tmp.resize(m);
+    at.assign((size_t)n + 1, 0);
+    auto pass = [&](const std::vector<Arc> &from, std::vector<Arc> &to, int shift) {
+        std::fill(at.begin(), at.end(), 0);
+        for (const Arc &a : from) at[(size_t)((a.key >> shift) & 0xffffffffu) + 1]++;
+        for (int v = 0; v < n; ++v) at[(size_t)v + 1] += at[v];
+        for (const Arc &a : from) to[(size_t)at[(size_t)((a.key >> shift) & 0xffffffffu)]++] = a;
+    };
+    pass(arcs, tmp, 0);    // by target
+    pass(tmp, arcs, 32);   // by source, stable: rows stay sorted by target
+    r.ptr.assign((size_t)n + 1, 0);
+    r.col.clear();
+    r.lab.clear();
+    r.col.reserve(m);
+    r.lab.reserve(m);
+    for (size_t i = 0; i < m; ++i) {
+        if (i > 0 && arcs[i - 1].key == arcs[i].key) {
+            if (arcs[i - 1].lab != arcs[i].lab) return false;   // repeated edge, other label
             continue;
         }
-        arcs[w++] = arcs[i];
-    }
-    arcs.resize(w);
-    r.ptr.assign((size_t)n + 1, 0);
-    r.col.resize(w);
-    r.lab.resize(w);
-    for (size_t i = 0; i < w; ++i) {
-        const int a = (int)(arcs[i].key >> 32);
-        r.ptr[(size_t)a + 1]++;
-        r.col[i] = (int32_t)(arcs[i].key & 0xffffffffu);
-        r.lab[i] = arcs[i].lab;
+        r.ptr[(size_t)(arcs[i].key >> 32) + 1]++;
+        r.col.push_back((int32_t)(arcs[i].key & 0xffffffffu));
+        r.lab.push_back(arcs[i].lab);
     }
     for (int v = 0; v < n; ++v) r.ptr[(size_t)v + 1] += r.ptr[v];
     return true;
@@ -130,7 +142,10 @@ bool build_graph(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, c
     if ((directed ? m : 2 * m) > INT32_MAX) { err = "more than 2^31-1 stored arcs"; return false; }
     g.n = n;
     g.directed = directed != 0;
-    std::vector<Arc> out, in;
+    g.any_elab = false;
+    static thread_local std::vector<Arc> out, in;   // per-thread scratch, reused
+    out.clear();
+    in.clear();
     out.reserve(g.directed ? (size_t)m : 2 * (size_t)m);
     if (g.directed) in.reserve((size_t)m);
     for (int64_t e = 0; e < m; ++e) {
@@ -142,6 +157,11 @@ bool build_graph(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, c
         out.push_back({(uint64_t)(uint32_t)a << 32 | (uint32_t)b, l});
         if (g.directed) in.push_back({(uint64_t)(uint32_t)b << 32 | (uint32_t)a, l});
         else out.push_back({(uint64_t)(uint32_t)b << 32 | (uint32_t)a, l});
+    }
+    if (!g.directed) {   // no in-rows (and none left from an earlier load through this scratch)
+        g.in.ptr.clear();
+        g.in.col.clear();
+        g.in.lab.clear();
     }
     if (!rows_from_arcs(n, out, g.out) || (g.directed && !rows_from_arcs(n, in, g.in))) {
         err = "repeated edge with a different label";
@@ -247,6 +267,17 @@ struct Workspace {
     }
 };
 
+// Device buffers of target ingest, kept by the context and reused by every load.
+struct IngestWs {
+    DevBuf src, dst, elab, vlab, cnt_out, cnt_in, fill_out, fill_in, off_out, off_in, key_out, key_in, scratch, ucnt,
+        uoff, long_rows, small, scan_tmp;
+    void release() {
+        for (DevBuf *b : {&src, &dst, &elab, &vlab, &cnt_out, &cnt_in, &fill_out, &fill_in, &off_out, &off_in, &key_out,
+                          &key_in, &scratch, &ucnt, &uoff, &long_rows, &small, &scan_tmp})
+            b->release();
+    }
+};
+
 struct ServeReq;
 
 }  // namespace
@@ -264,6 +295,8 @@ struct sge_ctx {
     int *cancel_host = nullptr;  // mapped pinned word
     int *cancel_dev = nullptr;
     Workspace ws;
+    IngestWs ing;
+    std::mutex ingest_mu;        // one target ingest at a time uses `ing`
     // serving
     std::mutex smu;
     std::condition_variable scv;
@@ -1374,6 +1407,7 @@ void sge_destroy(sge_ctx *ctx) {
     for (auto &kv : ctx->targets) kv.second->release();
     for (auto &kv : ctx->patterns) kv.second->release();
     ctx->ws.release();
+    ctx->ing.release();
     if (ctx->cancel_host) cudaFreeHost(ctx->cancel_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1382,43 +1416,118 @@ void sge_destroy(sge_ctx *ctx) {
 sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                            const int32_t *vlabel, const int32_t *elabel, int32_t directed, int32_t *target_id) {
     if (!ctx || !target_id) return SGE_ERR_ARG;
-    Built g;
-    sge_status rc = load_graph_common(ctx, n, m, src, dst, vlabel, elabel, directed, g);
-    if (rc != SGE_OK) return rc;
+    if (n < 0 || m < 0) return fail(ctx, SGE_ERR_ARG, "negative vertex or edge count");
+    if (m > 0 && (!src || !dst)) return fail(ctx, SGE_ERR_ARG, "null edge arrays");
+    if (n > 0 && !vlabel) return fail(ctx, SGE_ERR_ARG, "null vertex-label array");
+    const long long arcs = directed ? m : 2 * m;   // stored arcs before repeats merge
+    if (arcs > INT32_MAX) return fail(ctx, SGE_ERR_ARG, "more than 2^31-1 stored arcs");
+    const double t_in = now_ms();
     cudaSetDevice(ctx->device);
     cudaStream_t st = ctx->stream;
+    std::lock_guard<std::mutex> ig(ctx->ingest_mu);
+    IngestWs &I = ctx->ing;
     auto T = std::make_unique<TargetRec>();
     T->n = n;
-    T->directed = g.directed;
-    T->any_elab = g.any_elab;
-    T->nnz = (long long)g.out.col.size();
+    T->directed = directed != 0;
     T->dw = std::max(1, (n + 63) / 64);
-    std::vector<int2> vld((size_t)n);
-    for (int v = 0; v < n; ++v) vld[v] = make_int2(g.vlab[v], g.odeg[v]);
-    CK(upload(T->rowptr, g.out.ptr, st), "upload rowptr");
-    CK(upload(T->col, g.out.col, st), "upload col");
-    CK(upload(T->elab, g.out.lab, st), "upload elab");
-    CK(upload(T->vld, vld, st), "upload vertex info");
-    if (g.directed) {
-        CK(upload(T->irowptr, g.in.ptr, st), "upload in-rowptr");
-        CK(upload(T->icol, g.in.col, st), "upload in-col");
-        CK(upload(T->ielab, g.in.lab, st), "upload in-elab");
-        CK(upload(T->indeg, g.ideg, st), "upload in-degree");
-    } else if (n > 0 && n <= BITSET_MAX_N) {
-        std::vector<uint64_t> bits((size_t)n * T->dw, 0);
-        for (int v = 0; v < n; ++v)
-            for (int e = g.out.ptr[v]; e < g.out.ptr[v + 1]; ++e) {
-                const int w = g.out.col[e];
-                bits[(size_t)v * T->dw + (w >> 6)] |= 1ull << (w & 63);
-            }
-        CK(upload(T->adj, bits, st), "upload adjacency bitset");
-    } else if (n > BITSET_MAX_N) {
+    const size_t n1 = (size_t)n + 1;
+    // the caller's arrays, once
+    CK(I.src.ensure(std::max<long long>(m, 1) * 4), "alloc ingest");
+    CK(I.dst.ensure(std::max<long long>(m, 1) * 4), "alloc ingest");
+    CK(I.vlab.ensure(std::max<size_t>(n, 1) * 4), "alloc ingest");
+    if (m > 0) {
+        CK(cudaMemcpyAsync(I.src.p, src, (size_t)m * 4, cudaMemcpyHostToDevice, st), "upload edges");
+        CK(cudaMemcpyAsync(I.dst.p, dst, (size_t)m * 4, cudaMemcpyHostToDevice, st), "upload edges");
+    }
+    if (n > 0) CK(cudaMemcpyAsync(I.vlab.p, vlabel, (size_t)n * 4, cudaMemcpyHostToDevice, st), "upload labels");
+    const int32_t *d_elab = nullptr;
+    if (elabel && m > 0) {
+        CK(I.elab.ensure((size_t)m * 4), "alloc ingest");
+        CK(cudaMemcpyAsync(I.elab.p, elabel, (size_t)m * 4, cudaMemcpyHostToDevice, st), "upload edge labels");
+        d_elab = I.elab.as<int32_t>();
+    }
+    // scratch: per-vertex counters and offsets, arc keys
+    const size_t nv = std::max<size_t>(n, 1);
+    for (DevBuf *b : {&I.cnt_out, &I.cnt_in, &I.fill_out, &I.fill_in, &I.ucnt, &I.long_rows})
+        CK(b->ensure(nv * 4), "alloc ingest");
+    for (DevBuf *b : {&I.off_out, &I.off_in, &I.uoff}) CK(b->ensure(n1 * 8), "alloc ingest");
+    CK(I.key_out.ensure((size_t)std::max<long long>(arcs, 1) * 8), "alloc ingest");
+    CK(I.scratch.ensure((size_t)std::max<long long>(arcs, 1) * 8), "alloc ingest");
+    if (directed) CK(I.key_in.ensure((size_t)std::max<long long>(m, 1) * 8), "alloc ingest");
+    CK(I.small.ensure(64), "alloc ingest");
+    CK(I.scan_tmp.ensure(scan_tmp_bytes(n)), "alloc ingest");
+    int *flags = I.small.as<int>();
+    int32_t *nlong = I.small.as<int32_t>() + 1;   // [1] out rows, [2] in rows
+    CK(cudaMemsetAsync(I.small.p, 0, 64, st), "clear ingest");
+    for (DevBuf *b : {&I.cnt_out, &I.cnt_in, &I.fill_out, &I.fill_in})
+        CK(cudaMemsetAsync(b->p, 0, nv * 4, st), "clear ingest");
+    CK(launch_ingest_count(I.src.as<int32_t>(), I.dst.as<int32_t>(), d_elab, m, n, directed ? 1 : 0,
+                           I.cnt_out.as<int32_t>(), I.cnt_in.as<int32_t>(), flags, st), "ingest count");
+    CK(launch_scan(I.cnt_out.as<int32_t>(), I.off_out.as<long long>(), n, I.off_out.as<long long>() + n,
+                   I.scan_tmp.p, I.scan_tmp.cap, st), "ingest scan");
+    if (directed)
+        CK(launch_scan(I.cnt_in.as<int32_t>(), I.off_in.as<long long>(), n, I.off_in.as<long long>() + n,
+                       I.scan_tmp.p, I.scan_tmp.cap, st), "ingest scan");
+    CK(launch_ingest_scatter(I.src.as<int32_t>(), I.dst.as<int32_t>(), d_elab, m, n, directed ? 1 : 0,
+                             I.off_out.as<long long>(), I.off_in.as<long long>(), I.fill_out.as<int32_t>(),
+                             I.fill_in.as<int32_t>(), I.key_out.as<uint64_t>(), I.key_in.as<uint64_t>(), st),
+       "ingest scatter");
+    // sort and merge the rows of one direction, then compact them into the target's CSR
+    auto rows = [&](DevBuf &off, DevBuf &keys, int32_t *nl, DevBuf &rowptr, DevBuf &colb, DevBuf &labb,
+                    long long cap) -> cudaError_t {
+        cudaError_t e = launch_ingest_rows(off.as<long long>(), n, keys.as<uint64_t>(), I.scratch.as<uint64_t>(),
+                                           I.ucnt.as<int32_t>(), I.long_rows.as<int32_t>(), nl, flags, ctx->sms, st);
+        if (e == cudaSuccess)
+            e = launch_scan(I.ucnt.as<int32_t>(), I.uoff.as<long long>(), n, I.uoff.as<long long>() + n,
+                            I.scan_tmp.p, I.scan_tmp.cap, st);
+        if (e == cudaSuccess) e = rowptr.ensure(n1 * 4);
+        if (e == cudaSuccess) e = colb.ensure((size_t)std::max<long long>(cap, 1) * 4);
+        if (e == cudaSuccess) e = labb.ensure((size_t)std::max<long long>(cap, 1) * 4);
+        if (e == cudaSuccess)
+            e = launch_ingest_compact(off.as<long long>(), I.uoff.as<long long>(), I.ucnt.as<int32_t>(),
+                                      I.uoff.as<long long>() + n, keys.as<uint64_t>(), n, rowptr.as<int32_t>(),
+                                      colb.as<int32_t>(), labb.as<int32_t>(), st);
+        return e;
+    };
+    long long nnz[2] = {0, 0};
+    CK(rows(I.off_out, I.key_out, nlong, T->rowptr, T->col, T->elab, arcs), "ingest rows");
+    CK(cudaMemcpyAsync(&nnz[0], I.uoff.as<long long>() + n, 8, cudaMemcpyDeviceToHost, st), "read arc count");
+    if (directed) {
+        CK(rows(I.off_in, I.key_in, nlong + 1, T->irowptr, T->icol, T->ielab, m), "ingest in-rows");
+        CK(cudaMemcpyAsync(&nnz[1], I.uoff.as<long long>() + n, 8, cudaMemcpyDeviceToHost, st), "read arc count");
+        CK(T->indeg.ensure(nv * 4), "alloc in-degree");
+        CK(launch_ingest_degree(T->irowptr.as<int32_t>(), n, T->indeg.as<int32_t>(), st), "in-degree");
+    }
+    CK(T->vld.ensure(nv * sizeof(int2)), "alloc vertex info");
+    CK(launch_make_vld(T->rowptr.as<int32_t>(), I.vlab.as<int32_t>(), T->vld.as<int2>(), n, st), "vertex info");
+    if (!directed && n > 0 && n <= BITSET_MAX_N) {
+        CK(T->adj.ensure((size_t)n * T->dw * 8), "alloc adjacency bitset");
+        CK(cudaMemsetAsync(T->adj.p, 0, (size_t)n * T->dw * 8, st), "clear adjacency bitset");
+        CK(launch_ingest_bits(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), n, T->dw, T->adj.as<uint64_t>(), st),
+           "adjacency bitset");
+    }
+    int hflags = 0;
+    CK(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st), "read ingest flags");
+    CK(cudaStreamSynchronize(st), "target ingest");
+    const char *bad = (hflags & ING_RANGE) ? "edge endpoint out of range"
+                      : (hflags & ING_LOOP) ? "self-loop"
+                      : (hflags & ING_LABEL) ? "repeated edge with a different label" : nullptr;
+    if (bad) {
+        T->release();
+        return fail(ctx, SGE_ERR_ARG, bad);
+    }
+    T->any_elab = (hflags & ING_ELAB) != 0;
+    T->nnz = nnz[0];
+    if (!directed && n > BITSET_MAX_N) {
         // hub rows: the highest-degree vertices get a bitset row (rule 4 becomes one bit test)
+        std::vector<int32_t> ptr(n1);
+        CK(cudaMemcpy(ptr.data(), T->rowptr.p, n1 * 4, cudaMemcpyDeviceToHost), "read row offsets");
         std::vector<int32_t> order;
         for (int v = 0; v < n; ++v)
-            if (g.odeg[v] >= HUB_MIN_DEGREE) order.push_back(v);
+            if (ptr[v + 1] - ptr[v] >= HUB_MIN_DEGREE) order.push_back(v);
         std::sort(order.begin(), order.end(), [&](int a, int b) {
-            return g.odeg[a] != g.odeg[b] ? g.odeg[a] > g.odeg[b] : a < b;
+            const int da = ptr[a + 1] - ptr[a], db = ptr[b + 1] - ptr[b];
+            return da != db ? da > db : a < b;
         });
         const long long max_hubs = HUB_BYTES / ((long long)T->dw * 8);
         if ((long long)order.size() > max_hubs) order.resize((size_t)max_hubs);
@@ -1430,9 +1539,10 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
             CK(T->hub_bits.ensure(order.size() * (size_t)T->dw * 8), "alloc hub rows");
             CK(launch_build_hubs(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), T->hub_list.as<int32_t>(),
                                  (int)order.size(), T->dw, T->hub_bits.as<uint64_t>(), st), "hub rows");
+            CK(cudaStreamSynchronize(st), "hub rows");
         }
     }
-    CK(cudaStreamSynchronize(st), "target upload");
+    if (trace_on()) std::fprintf(stderr, "[sge] target n %d: ingested on the device in %.3f ms\n", n, now_ms() - t_in);
     std::lock_guard<std::mutex> gd(ctx->mu);
     const int id = ctx->next_target++;
     ctx->targets[id] = std::move(T);

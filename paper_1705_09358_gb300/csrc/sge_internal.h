@@ -211,4 +211,23 @@ cudaError_t launch_build_hubs(const int32_t *rowptr, const int32_t *col, const i
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
 cudaError_t launch_make_vld(const int32_t *rowptr, const int32_t *vlabel, int2 *vld, int n, cudaStream_t st);
 
+// Target ingest on the device (sge_ingest.cu).  Error bits of the flags word:
+constexpr int ING_RANGE = 1;   // an endpoint outside [0, n)
+constexpr int ING_LOOP = 2;    // a self-loop
+constexpr int ING_LABEL = 4;   // a repeated edge with another label
+constexpr int ING_ELAB = 8;    // (not an error) some edge label is nonzero
+cudaError_t launch_ingest_count(const int32_t *src, const int32_t *dst, const int32_t *elab, long long m, int n,
+                                int directed, int32_t *cnt_out, int32_t *cnt_in, int *flags, cudaStream_t st);
+cudaError_t launch_ingest_scatter(const int32_t *src, const int32_t *dst, const int32_t *elab, long long m, int n,
+                                  int directed, const long long *off_out, const long long *off_in, int32_t *fill_out,
+                                  int32_t *fill_in, uint64_t *key_out, uint64_t *key_in, cudaStream_t st);
+cudaError_t launch_ingest_rows(const long long *off, int n, uint64_t *keys, uint64_t *scratch, int32_t *ucnt,
+                               int32_t *long_rows, int32_t *nlong, int *flags, int sms, cudaStream_t st);
+cudaError_t launch_ingest_compact(const long long *off, const long long *uoff, const int32_t *ucnt,
+                                  const long long *utotal, const uint64_t *keys, int n, int32_t *rowptr, int32_t *col,
+                                  int32_t *lab, cudaStream_t st);
+cudaError_t launch_ingest_degree(const int32_t *rowptr, int n, int32_t *deg, cudaStream_t st);
+cudaError_t launch_ingest_bits(const int32_t *rowptr, const int32_t *col, int n, int dw, uint64_t *bits,
+                               cudaStream_t st);
+
 }  // namespace sge
