@@ -37,6 +37,7 @@ constexpr int HUB_MIN_DEGREE = 24;               // larger targets: bitset rows 
 constexpr long long HUB_BYTES = 512ll << 20;     // ... within this much device memory
 constexpr long long FRONTIER_MAX_INTS = 1ll << 27;  // 512 MB per frontier buffer
 constexpr int POOL_CELLS = 1 << 15;
+constexpr long long CAND_MAX = 1ll << 28;   // most listed domain candidates per launch group (1 GiB)
 constexpr int ROOT_CHUNK = 1024;                 // root candidates per root range frame
 
 // Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
@@ -252,13 +253,15 @@ struct PatternRec {
 
 // Scratch of one launch sequence (the serving scheduler has one per slot).
 struct Workspace {
-    DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag;
+    DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag, dent, deoff, vchg, cand,
+        ctask;
     DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
     DevBuf mbuf, ckpt, wtrace;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void release() {
         for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
+                          &dent, &deoff, &vchg, &cand, &ctask,
                           &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt, &wtrace})
             b->release();
         if (ev0) cudaEventDestroy(ev0);
@@ -623,25 +626,130 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             any_fc = any_fc || jobs[q].algo == SGE_RIDS_SI_FC;
         }
         if (any_rids) {
-            // arc consistency to its fixpoint, alternating with forward checking
+            // arc consistency to its fixpoint, alternating with forward checking.  A sweep
+            // re-checks D(v) only if the domain of a pattern neighbour of v shrank in the
+            // previous sweep (the first sweep of a round checks every RI-DS vertex).
+            std::vector<int> gjob((size_t)nverts), gv_v((size_t)nverts);
+            for (int fj = 0; fj < nf; ++fj) {
+                const Job &J = jobs[fjobs[fj]];
+                for (int v = 0; v < J.p->k; ++v) {
+                    gjob[(size_t)J.vert_off + v] = fj;
+                    gv_v[(size_t)J.vert_off + v] = v;
+                }
+            }
+            std::vector<unsigned char> dirty((size_t)nverts, 0), vchg((size_t)nverts, 0);
+            auto mark_all = [&]() {
+                for (long long g = 0; g < nverts; ++g) dirty[(size_t)g] = jobs[fjobs[gjob[(size_t)g]]].algo != SGE_RI;
+            };
+            CK(W.vchg.ensure((size_t)std::max<long long>(nverts, 1)), "alloc domain flags");
+            // explicit candidate lists of the RI-DS domains, so that a sweep runs one thread per
+            // candidate instead of one warp per 64-target word (most words of a large target's
+            // domains hold few candidates); word sweeps when the lists would be too large
+            std::vector<long long> csize((size_t)nverts, 0), cstart((size_t)nverts, 0);
+            long long ncand = 0;
+            {
+                CK(launch_domain_sizes(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts,
+                                       W.sizes.as<long long>(), st), "domain sizes");
+                ++launches;
+                CK(cudaMemcpyAsync(csize.data(), W.sizes.p, (size_t)nverts * 8, cudaMemcpyDeviceToHost, st),
+                   "read sizes");
+                CK(cudaStreamSynchronize(st), "sizes sync");
+                for (long long g = 0; g < nverts; ++g) {
+                    if (jobs[fjobs[gjob[(size_t)g]]].algo == SGE_RI) csize[(size_t)g] = 0;
+                    cstart[(size_t)g] = ncand;
+                    ncand += csize[(size_t)g];
+                }
+            }
+            const bool cand_mode = ncand > 0 && ncand <= CAND_MAX;
+            if (cand_mode) {
+                std::vector<int> tj, tv, to;
+                for (long long g = 0; g < nverts; ++g)
+                    if (csize[(size_t)g] > 0) {
+                        tj.push_back(gjob[(size_t)g]);
+                        tv.push_back(gv_v[(size_t)g]);
+                        to.push_back((int)cstart[(size_t)g]);
+                    }
+                std::vector<int> tall(tj);
+                tall.insert(tall.end(), tv.begin(), tv.end());
+                tall.insert(tall.end(), to.begin(), to.end());
+                CK(upload(W.ctask, tall, st), "upload candidate tasks");
+                CK(W.cand.ensure((size_t)ncand * 4), "alloc candidate lists");
+                const int nt = (int)tj.size();
+                CK(launch_domain_lists(W.fjobs.as<JobDesc>(), W.ctask.as<int>(), W.ctask.as<int>() + nt,
+                                       W.ctask.as<int>() + 2 * nt, nt, W.cand.as<int32_t>(), st), "candidate lists");
+                ++launches;
+            }
+            // the neighbours of every shrunk domain (vchg) are re-checked next
+            auto mark_neighbours = [&]() {
+                std::fill(dirty.begin(), dirty.end(), 0);
+                for (long long g = 0; g < nverts; ++g) {
+                    if (!vchg[(size_t)g]) continue;
+                    const Job &J = jobs[fjobs[gjob[(size_t)g]]];
+                    if (J.algo == SGE_RI) continue;
+                    const int v = gv_v[(size_t)g];
+                    for (int w = 0; w < 2; ++w)
+                        for (uint64_t b = J.p->nb[(size_t)v * 2 + w]; b; b &= b - 1)
+                            dirty[(size_t)J.vert_off + 64 * w + __builtin_ctzll(b)] = 1;
+                }
+            };
+            std::vector<int4> ent;
+            std::vector<long long> eoff;
+            mark_all();
             for (int outer = 0; outer < 100000; ++outer) {
-                int changed = 1;
-                for (int sweep = 0; changed && sweep < 1000000; ++sweep) {
+                for (int sweep = 0; sweep < 1000000; ++sweep) {
+                    ent.clear();
+                    eoff.clear();
+                    long long units = 0;
+                    for (long long g = 0; g < nverts; ++g)
+                        if (dirty[(size_t)g]) {
+                            const int fj = gjob[(size_t)g];
+                            if (cand_mode && csize[(size_t)g] == 0) continue;
+                            ent.push_back(make_int4(fj, gv_v[(size_t)g], (int)g, (int)cstart[(size_t)g]));
+                            eoff.push_back(units);
+                            units += cand_mode ? csize[(size_t)g] : jobs[fjobs[fj]].t->dw;
+                        }
+                    if (ent.empty()) break;
+                    eoff.push_back(units);
+                    const double ts = now_ms();
+                    CK(upload(W.dent, ent, st), "upload domain entries");
+                    CK(upload(W.deoff, eoff, st), "upload domain entries");
                     CK(cudaMemsetAsync(W.flag.p, 0, sizeof(int), st), "clear flag");
-                    CK(launch_domain_ac(W.fjobs.as<JobDesc>(), W.unit_off.as<long long>(), nf, nunits,
-                                        W.flag.as<int>(), st), "domain ac");
+                    CK(cudaMemsetAsync(W.vchg.p, 0, (size_t)nverts, st), "clear domain flags");
+                    if (cand_mode)
+                        CK(launch_domain_ac_cand(W.fjobs.as<JobDesc>(), W.dent.as<int4>(), W.deoff.as<long long>(),
+                                                 (int)ent.size(), units, W.cand.as<int32_t>(), W.flag.as<int>(),
+                                                 W.vchg.as<unsigned char>(), st),
+                           "domain ac");
+                    else
+                        CK(launch_domain_ac(W.fjobs.as<JobDesc>(), W.dent.as<int4>(), W.deoff.as<long long>(),
+                                            (int)ent.size(), units, W.flag.as<int>(), W.vchg.as<unsigned char>(), st),
+                           "domain ac");
                     ++launches;
-                    CK(cudaMemcpyAsync(&changed, W.flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+                    CK(cudaMemcpyAsync(vchg.data(), W.vchg.p, (size_t)nverts, cudaMemcpyDeviceToHost, st),
+                       "read domain flags");
                     CK(cudaStreamSynchronize(st), "ac sync");
+                    if (trace_on())
+                        std::fprintf(stderr, "[sge] ac sweep %d (round %d): %.3f ms, %zu vertices, %lld units\n", sweep,
+                                     outer, now_ms() - ts, ent.size(), units);
+                    mark_neighbours();
                 }
                 if (!any_fc) break;
                 int fchanged = 0;
+                const double tf = now_ms();
                 CK(cudaMemsetAsync(W.flag.p, 0, sizeof(int), st), "clear flag");
-                CK(launch_domain_fc(W.fjobs.as<JobDesc>(), nf, W.flag.as<int>(), st), "domain fc");
-                ++launches;
+                CK(cudaMemsetAsync(W.vchg.p, 0, (size_t)nverts, st), "clear domain flags");
+                CK(launch_domain_sizes(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts,
+                                       W.sizes.as<long long>(), st), "domain sizes");
+                CK(launch_domain_fc(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), W.sizes.as<long long>(), nf,
+                                    W.flag.as<int>(), W.vchg.as<unsigned char>(), st), "domain fc");
+                launches += 2;
                 CK(cudaMemcpyAsync(&fchanged, W.flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+                CK(cudaMemcpyAsync(vchg.data(), W.vchg.p, (size_t)nverts, cudaMemcpyDeviceToHost, st),
+                   "read domain flags");
                 CK(cudaStreamSynchronize(st), "fc sync");
+                if (trace_on()) std::fprintf(stderr, "[sge] fc round %d: %.3f ms\n", outer, now_ms() - tf);
                 if (!fchanged) break;
+                mark_neighbours();   // only neighbours of domains that forward checking shrank
             }
         }
         CK(launch_domain_sizes(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts,

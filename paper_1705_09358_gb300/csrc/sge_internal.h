@@ -166,9 +166,13 @@ inline void bind_control(SearchCtl &C, void *block) {
 
 cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
                                long long nunits, cudaStream_t st);
-cudaError_t launch_domain_ac(const JobDesc *jobs, const long long *unit_off, int njobs,
-                             long long nunits, int *changed, cudaStream_t st);
-cudaError_t launch_domain_fc(const JobDesc *jobs, int njobs, int *changed, cudaStream_t st);
+cudaError_t launch_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff, int nent,
+                                  long long ncand, int32_t *cand, int *changed, unsigned char *vchanged,
+                                  cudaStream_t st);
+cudaError_t launch_domain_ac(const JobDesc *jobs, const int4 *ent, const long long *eoff, int nent, long long nunits,
+                             int *changed, unsigned char *vchanged, cudaStream_t st);
+cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, const long long *sizes, int njobs,
+                             int *changed, unsigned char *vchanged, cudaStream_t st);
 cudaError_t launch_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
                                 long long nverts, long long *sizes, cudaStream_t st);
 cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert,

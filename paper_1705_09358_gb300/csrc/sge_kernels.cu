@@ -217,21 +217,79 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
     if (lane == 0) J.filt[(size_t)v * J.t.dw + q] = word;
 }
 
+// Arc consistency of one candidate (Section 4): does target vertex t keep,
+// for every pattern edge at v, a compatible target edge into the other
+// endpoint's domain?
+__device__ bool ac_supported(const JobDesc &J, int v, int t, bool DIR, bool chk) {
+    const int dw = J.t.dw;
+    for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) {
+        const int uu = J.p.col[e], bl = chk ? J.p.elab[e] : 0;
+        const uint64_t *Du = J.filt + (size_t)uu * dw;
+        bool found = false;
+        for (int f = __ldg(J.t.rowptr + t), fe = __ldg(J.t.rowptr + t + 1); f < fe; ++f) {
+            const int y = __ldg(J.t.col + f);
+            if ((!chk || __ldg(J.t.elab + f) == bl) && ((Du[y >> 6] >> (y & 63)) & 1ull)) { found = true; break; }
+        }
+        if (!found) return false;
+    }
+    if (DIR) {
+        for (int e = J.p.irowptr[v]; e < J.p.irowptr[v + 1]; ++e) {
+            const int uu = J.p.icol[e], bl = chk ? J.p.ielab[e] : 0;
+            const uint64_t *Du = J.filt + (size_t)uu * dw;
+            bool found = false;
+            for (int f = __ldg(J.t.irowptr + t), fe = __ldg(J.t.irowptr + t + 1); f < fe; ++f) {
+                const int y = __ldg(J.t.icol + f);
+                if ((!chk || __ldg(J.t.ielab + f) == bl) && ((Du[y >> 6] >> (y & 63)) & 1ull)) { found = true; break; }
+            }
+            if (!found) return false;
+        }
+    }
+    return true;
+}
+
+// The same sweep over explicit candidate lists: one thread per listed
+// candidate of the listed entries {job, pattern vertex, global vertex,
+// list start}; a removed candidate is cleared from D(v) and its list slot.
+__global__ void __launch_bounds__(BLOCK) k_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff,
+                                                          int nent, long long ncand, int32_t *cand, int *changed,
+                                                          unsigned char *vchanged) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= ncand) return;
+    const int i = find_job(eoff, nent, x);
+    const int4 E = ent[i];
+    const JobDesc &J = jobs[E.x];
+    int32_t *slot = cand + (long long)E.w + (x - eoff[i]);
+    const int t = *slot;
+    if (t < 0) return;
+    uint64_t *wp = J.filt + (size_t)E.y * J.t.dw + (t >> 6);
+    const uint64_t bit = 1ull << (t & 63);
+    if (!(*wp & bit)) { *slot = -1; return; }    // removed by forward checking
+    if (ac_supported(J, E.y, t, (J.flags & JOB_DIRECTED) != 0, (J.flags & JOB_ELAB) != 0)) return;
+    atomicAnd((unsigned long long *)wp, ~bit);
+    *slot = -1;
+    *changed = 1;
+    vchanged[E.z] = 1;
+}
+
 // One arc-consistency sweep (Section 4): drop t from D(v) when a pattern
 // edge at v has no compatible target edge at t into the other endpoint's
 // domain.  Removals are applied in place (monotone), so sweeping until no
-// word changes reaches the unique greatest fixpoint.
-__global__ void __launch_bounds__(BLOCK) k_domain_ac(const JobDesc *jobs, const long long *unit_off, int njobs,
-                                                     long long nunits, int *changed) {
+// word changes reaches the unique greatest fixpoint.  A sweep visits only
+// the listed (job, pattern vertex) entries -- those with a neighbour whose
+// domain shrank in the previous sweep -- one warp per 64-target word, and
+// marks every domain it shrinks in vchanged.
+__global__ void __launch_bounds__(BLOCK) k_domain_ac(const JobDesc *jobs, const int4 *ent, const long long *eoff,
+                                                     int nent, long long nunits, int *changed,
+                                                     unsigned char *vchanged) {
     const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (u >= nunits) return;
-    const int j = find_job(unit_off, njobs, u);
-    const JobDesc &J = jobs[j];
+    const int i = find_job(eoff, nent, u);
+    const int4 E = ent[i];   // {job, pattern vertex, global vertex index, 0}
+    const JobDesc &J = jobs[E.x];
     if (J.filt == nullptr || !(J.flags & JOB_RIDS)) return;
     const bool DIR = (J.flags & JOB_DIRECTED) != 0;
-    const long long local = u - unit_off[j];
-    const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
+    const int v = E.y, q = (int)(u - eoff[i]);
     uint64_t *wp = J.filt + (size_t)v * J.t.dw + q;
     const uint64_t word = *wp;
     if (word == 0) return;
@@ -272,56 +330,71 @@ __global__ void __launch_bounds__(BLOCK) k_domain_ac(const JobDesc *jobs, const 
     if (lane == 0 && keep != word) {
         atomicAnd((unsigned long long *)wp, keep);
         *changed = 1;
+        vchanged[E.z] = 1;
     }
 }
 
 // Forward checking (Section 4.2): the target node of a singleton domain is
-// removed from every other domain, repeated until no singleton removes
-// anything.  One block per job.
-__global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, int *changed) {
-    __shared__ int cnt[KMAX];
+// removed from every other domain, repeated until no new singleton appears.
+// One block per job, starting from the domain sizes: each round takes the
+// singletons not yet propagated, finds each one's element (one warp scans
+// its words), and clears that element's word in every other domain,
+// counting the sizes down (all singletons of a round propagate together).
+__global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const long long *vert_off,
+                                                     const long long *sizes, int *changed, unsigned char *vchanged) {
+    __shared__ int size[KMAX];
     __shared__ int elem[KMAX];
-    __shared__ int sing_t[KMAX];
-    __shared__ int sing_u[KMAX];
-    __shared__ int nsing;
-    __shared__ int any;
+    __shared__ unsigned char done[KMAX];
+    __shared__ int newu[KMAX];
+    __shared__ int nnew;
     const JobDesc &J = jobs[blockIdx.x];
     if (J.filt == nullptr || !(J.flags & JOB_FC)) return;
     const int k = J.k, dw = J.t.dw;
-    const long long words = (long long)k * dw;
-    for (int round = 0; round < 4 * KMAX + 8; ++round) {
-        for (int v = threadIdx.x; v < k; v += blockDim.x) { cnt[v] = 0; elem[v] = -1; }
-        if (threadIdx.x == 0) { nsing = 0; any = 0; }
-        __syncthreads();
-        for (long long x = threadIdx.x; x < words; x += blockDim.x) {
-            const uint64_t w = J.filt[x];
-            if (w) {
-                const int v = (int)(x / dw), q = (int)(x % dw);
-                atomicAdd(&cnt[v], __popcll(w));
-                elem[v] = q * 64 + __ffsll((long long)w) - 1;
-            }
-        }
+    const long long vo = vert_off[blockIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int v = threadIdx.x; v < k; v += blockDim.x) {
+        size[v] = (int)sizes[vo + v];   // exact, counted down on every removal
+        done[v] = 0;
+    }
+    __syncthreads();
+    for (int round = 0; round <= k; ++round) {
+        if (threadIdx.x == 0) nnew = 0;
         __syncthreads();
         for (int v = threadIdx.x; v < k; v += blockDim.x)
-            if (cnt[v] == 1) {
-                const int s = atomicAdd(&nsing, 1);
-                sing_u[s] = v;
-                sing_t[s] = elem[v];
+            if (size[v] == 1 && !done[v]) {
+                done[v] = 1;
+                newu[atomicAdd(&nnew, 1)] = v;
             }
         __syncthreads();
-        const int ns = nsing;
-        if (ns == 0) break;
-        for (long long x = threadIdx.x; x < words; x += blockDim.x) {
-            const int v = (int)(x / dw), q = (int)(x % dw);
-            uint64_t mask = 0;
-            for (int s = 0; s < ns; ++s)
-                if (sing_u[s] != v && (sing_t[s] >> 6) == q) mask |= 1ull << (sing_t[s] & 63);
-            const uint64_t w = J.filt[x];
-            if (w & mask) { J.filt[x] = w & ~mask; any = 1; }
+        const int nn = nnew;
+        if (nn == 0) break;
+        for (int s = wid; s < nn; s += nwarps) {
+            const int u = newu[s];
+            int found = -1;
+            for (int q0 = 0; q0 < dw && found < 0; q0 += 32) {
+                const int q = q0 + lane;
+                const uint64_t w = q < dw ? J.filt[(size_t)u * dw + q] : 0ull;
+                const unsigned b = __ballot_sync(FULL, w != 0);
+                if (b) {
+                    const int L = __ffs(b) - 1;
+                    const uint64_t wl = __shfl_sync(FULL, w, L);
+                    found = (q0 + L) * 64 + __ffsll((long long)wl) - 1;
+                }
+            }
+            if (lane == 0) elem[u] = found;
         }
         __syncthreads();
-        if (!any) break;
-        if (threadIdx.x == 0) *changed = 1;
+        for (int x = threadIdx.x; x < nn * k; x += blockDim.x) {
+            const int u = newu[x / k], v = x % k, t = elem[u];
+            if (v == u || t < 0) continue;
+            unsigned long long *wp = reinterpret_cast<unsigned long long *>(J.filt + (size_t)v * dw + (t >> 6));
+            const unsigned long long bit = 1ull << (t & 63);
+            if (atomicAnd(wp, ~bit) & bit) {
+                atomicSub(&size[v], 1);
+                vchanged[vo + v] = 1;
+                *changed = 1;
+            }
+        }
         __syncthreads();
     }
 }
@@ -1717,16 +1790,26 @@ cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_domain_ac(const JobDesc *jobs, const long long *unit_off, int njobs, long long nunits,
-                             int *changed, cudaStream_t st) {
+cudaError_t launch_domain_ac(const JobDesc *jobs, const int4 *ent, const long long *eoff, int nent, long long nunits,
+                             int *changed, unsigned char *vchanged, cudaStream_t st) {
     if (nunits <= 0) return cudaSuccess;
-    k_domain_ac<<<grid_for(nunits), BLOCK, 0, st>>>(jobs, unit_off, njobs, nunits, changed);
+    k_domain_ac<<<grid_for(nunits), BLOCK, 0, st>>>(jobs, ent, eoff, nent, nunits, changed, vchanged);
     return cudaGetLastError();
 }
 
-cudaError_t launch_domain_fc(const JobDesc *jobs, int njobs, int *changed, cudaStream_t st) {
+cudaError_t launch_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff, int nent,
+                                  long long ncand, int32_t *cand, int *changed, unsigned char *vchanged,
+                                  cudaStream_t st) {
+    if (ncand <= 0) return cudaSuccess;
+    const long long blocks = (ncand + BLOCK - 1) / BLOCK;
+    k_domain_ac_cand<<<(unsigned)blocks, BLOCK, 0, st>>>(jobs, ent, eoff, nent, ncand, cand, changed, vchanged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, const long long *sizes, int njobs,
+                             int *changed, unsigned char *vchanged, cudaStream_t st) {
     if (njobs <= 0) return cudaSuccess;
-    k_domain_fc<<<njobs, BLOCK, 0, st>>>(jobs, changed);
+    k_domain_fc<<<njobs, BLOCK, 0, st>>>(jobs, vert_off, sizes, changed, vchanged);
     return cudaGetLastError();
 }
 
