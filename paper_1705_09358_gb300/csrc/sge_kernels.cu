@@ -1928,12 +1928,26 @@ size_t search_slab_bytes(int kernel, int kmax, int nwl, long long grid) {
     return (size_t)grid * WARPS_PER_BLOCK * bits_slab_words_per_warp(kmax, nwl) * sizeof(uint64_t);
 }
 
+// Let kernel `kern` take `smem` bytes of dynamic shared memory.  The limit is
+// a property of the kernel shared by every host thread that launches it, so
+// it is always raised to the device maximum, never set to one launch's need:
+// concurrent launches of different sizes (serving groups) cannot lower it
+// under one another.
+template <typename K>
+static cudaError_t allow_dynamic_smem(K kern, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if ((long long)smem > optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 template <typename K>
 static cudaError_t occupancy_of(K kern, size_t smem, int *occ) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_dynamic_smem(kern, smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, BLOCK, smem);
 }
 
@@ -1959,10 +1973,8 @@ static cudaError_t launch_persistent(K kern, const JobDesc *jobs, const SearchCt
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    e = allow_dynamic_smem(kern, smem);
+    if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BLOCK, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;

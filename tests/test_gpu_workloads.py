@@ -112,6 +112,31 @@ def test_serving_results_same_alone_and_in_mix():
         assert counters(E.count(tid, pids[i], algo=0)) == tuple(int(x) for x in want[i])
 
 
+def test_serving_concurrent_groups_of_different_sizes():
+    """Several scheduler threads launch groups of different pattern sizes at the
+    same time (their kernels need different amounts of shared memory); every
+    query must succeed with its own result, round after round."""
+    g = golden("cl100k")
+    t = workload("cl100k_target")
+    w = workload("cl100k")
+    E = engine()
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in w.patterns[:200]]
+    want = np.array(g["first_200"], dtype=np.uint64)
+    order = np.random.default_rng(5).permutation(len(pids))
+    for rnd in range(4):
+        tickets = []
+        for j, i in enumerate(order):
+            tickets.append((int(i), E.serve_submit(tid, pids[int(i)], algo=0)))
+            if j % 50 == 49:
+                time.sleep(0.0005 * rnd)
+        E.serve_drain()
+        for i, tk in tickets:
+            r = E.serve_poll(tk)
+            assert r is not None and r["status"] == 0, (rnd, i, r and r["status"])
+            assert counters(r) == tuple(int(x) for x in want[i]), (rnd, i)
+
+
 def test_cancel_from_another_thread():
     import paper_1705_09358_gb300 as sge
     E = engine()
