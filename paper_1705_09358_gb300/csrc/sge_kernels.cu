@@ -1385,8 +1385,7 @@ struct PosB {
 };
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
-    return round16((size_t)nwl * 32 * 8 +                   // used bitset
-                   8 +                                      // the frame's range (for checkpoints)
+    return round16(8 +                                      // the frame's range (for checkpoints)
                    (size_t)kmax * 4 +                       // M
                    (size_t)kmax * sizeof(PosB) +            // position table
                    (size_t)kmax * LIST_CAP * 2 +            // survivor lists
@@ -1405,7 +1404,6 @@ struct BitsJob {
 };
 
 struct BitsWarp {
-    uint64_t *used;
     int *M;
     PosB *tab;
     uint16_t *lst;     // [kmax][LIST_CAP]
@@ -1416,15 +1414,21 @@ struct BitsWarp {
 };
 
 template <int NWL>
-__device__ __forceinline__ void used_flip(uint64_t *used, int v) {
+__device__ __forceinline__ void used_flip(uint64_t (&used)[NWL], int v) {
+    // lane (q mod 32) holds word q of the used bitset in register used[q / 32]
     const int q = v >> 6;
-    if ((threadIdx.x & 31) == (q & 31)) used[(q >> 5) * 32 + (q & 31)] ^= 1ull << (v & 63);
+    if ((threadIdx.x & 31) == (q & 31)) {
+#pragma unroll
+        for (int w = 0; w < NWL; ++w)
+            if (w == (q >> 5)) used[w] ^= 1ull << (v & 63);
+    }
 }
 
 // Expand position i: compute S_i, count its survivors (the accepted nodes),
 // and either hash them as matches (leaf) or keep them as pending survivors.
 template <int NWL, bool RANGE = false>
-__device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W, int i, bool leaf,
+__device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W,
+                                           const uint64_t (&used)[NWL], int i, bool leaf,
                                            unsigned long long &st, unsigned long long &hs, unsigned long long &ab,
                                            int vlo = 0, int vhi = 0x7fffffff, bool count_len = true) {
     const int lane = threadIdx.x & 31;
@@ -1463,7 +1467,7 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
     int cnt = 0;
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
-        s[w] &= ~W.used[w * 32 + lane];
+        s[w] &= ~used[w];
         if (RANGE) {
             // a range frame: keep the candidates with vertex ids in [vlo, vhi]
             const int b0 = (lane + 32 * w) * 64;
@@ -1587,8 +1591,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
     BitsWarp W;
-    W.used = reinterpret_cast<uint64_t *>(base);
-    W.frange = reinterpret_cast<int *>(W.used + NWL * 32);
+    W.frange = reinterpret_cast<int *>(base);
     W.M = W.frange + 2;
     W.tab = reinterpret_cast<PosB *>(W.M + kmax);
     W.lst = reinterpret_cast<uint16_t *>(W.tab + kmax);
@@ -1596,6 +1599,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     W.tback = W.lcnt + kmax;
     W.slab = C.slab + ((size_t)blockIdx.x * WARPS_PER_BLOCK + wib) * bits_slab_words_per_warp(kmax, NWL);
     int *M = W.M;
+    uint64_t used[NWL];   // this lane's words of the used-vertex bitset (word lane + 32 w)
 
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
@@ -1627,9 +1631,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         unsigned long long st = 0, nd = 0, mt = 0, hs = 0, ab = 0;
         {
 #pragma unroll
-            for (int w = 0; w < NWL; ++w) W.used[w * 32 + lane] = 0ull;
+            for (int w = 0; w < NWL; ++w) used[w] = 0ull;
             __syncwarp();
-            for (int t = 0; t < d0; ++t) used_flip<NWL>(W.used, M[t]);
+            for (int t = 0; t < d0; ++t) used_flip<NWL>(used, M[t]);
             if (lane == 0) M[d0] = -1;
             __syncwarp();
         }
@@ -1661,8 +1665,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         if (lane == 0) { W.frange[0] = fr.beg; W.frange[1] = fr.end; }   // read back only by a checkpoint
         const bool count_len = fr.beg <= 0 && !fr.counted;
         const bool leaf0 = d0 == k - 1;
-        const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, d0, leaf0, st, hs, ab, vlo, vhi, count_len)
-                                   : bits_expand<NWL>(B, J, W, d0, leaf0, st, hs, ab);
+        const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, used, d0, leaf0, st, hs, ab, vlo, vhi, count_len)
+                                   : bits_expand<NWL>(B, J, W, used, d0, leaf0, st, hs, ab);
         if (!fr.counted) nd += c0;
         if (leaf0) {
             mt += c0;
@@ -1701,7 +1705,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     }
                 }
                 const int prev = M[lvl];
-                if (prev >= 0) used_flip<NWL>(W.used, prev);      // leave the previous choice at this level
+                if (prev >= 0) used_flip<NWL>(used, prev);      // leave the previous choice at this level
                 const int v = bits_next<NWL>(W, lvl);
                 if (v < 0) {
                     if (lane == 0) M[lvl] = -1;
@@ -1710,14 +1714,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     --lvl;
                     continue;
                 }
-                used_flip<NWL>(W.used, v);
+                used_flip<NWL>(used, v);
                 if (lane == 0) M[lvl] = v;
                 __syncwarp();
                 if (lvl + 1 == k - 1) {
-                    const int c = bits_expand<NWL>(B, J, W, lvl + 1, true, st, hs, ab);
+                    const int c = bits_expand<NWL>(B, J, W, used, lvl + 1, true, st, hs, ab);
                     nd += c; mt += c;
                 } else {
-                    nd += bits_expand<NWL>(B, J, W, lvl + 1, false, st, hs, ab);
+                    nd += bits_expand<NWL>(B, J, W, used, lvl + 1, false, st, hs, ab);
                     ++lvl;
                     if (lane == 0) M[lvl] = -1;
                     __syncwarp();
