@@ -51,6 +51,16 @@ class sge_result(C.Structure):
                 ("status", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
+# numpy view of sge_result: batched calls write their results straight into such an array
+RESULT_DTYPE = np.dtype(sge_result)
+
+
+def _result_array(n: int):
+    """(numpy array of n sge_result rows, pointer to pass to the library)."""
+    out = np.zeros(max(n, 1), dtype=RESULT_DTYPE)
+    return out, C.c_void_p(out.ctypes.data)
+
+
 SINK = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int32), C.c_int64, C.c_int32)
 
 _lib = None
@@ -201,13 +211,11 @@ def sge_count_batch(ctx, tids, pids, opts: sge_opts | None = None, check: bool =
     """Returns (rc, structured numpy array of sge_result rows)."""
     tids, pids = _i32(tids), _i32(pids)
     n = int(tids.shape[0])
-    out = (sge_result * max(n, 1))()
-    rc = load_library().sge_count_batch(ctx, n, _p(tids), _p(pids), C.byref(opts) if opts is not None else None,
-                                        C.cast(out, C.c_void_p))
+    out, ptr = _result_array(n)
+    rc = load_library().sge_count_batch(ctx, n, _p(tids), _p(pids), C.byref(opts) if opts is not None else None, ptr)
     if check:
         _check(ctx, rc, "sge_count_batch")
-    arr = np.ctypeslib.as_array(out)[:n] if n else np.zeros(0)
-    return int(rc), np.array(arr, copy=True)
+    return int(rc), out[:n]
 
 
 def _take_blob(ptr: C.c_void_p, nbytes: C.c_int64):
@@ -230,16 +238,15 @@ def sge_count_batch_ckpt(ctx, tids, pids, opts: sge_opts | None = None, check: b
     rows hold the counters so far and the checkpoint the work left."""
     tids, pids = _i32(tids), _i32(pids)
     n = int(tids.shape[0])
-    out = (sge_result * max(n, 1))()
+    out, optr = _result_array(n)
     ptr, nbytes = C.c_void_p(), C.c_int64(0)
     rc = load_library().sge_count_batch_ckpt(ctx, n, _p(tids), _p(pids),
                                              C.byref(opts) if opts is not None else None,
-                                             C.cast(out, C.c_void_p), C.byref(ptr), C.byref(nbytes))
+                                             optr, C.byref(ptr), C.byref(nbytes))
     blob = _take_blob(ptr, nbytes)
     if check and rc not in _STOPS:
         _check(ctx, rc, "sge_count_batch_ckpt")
-    arr = np.ctypeslib.as_array(out)[:n] if n else np.zeros(0)
-    return int(rc), np.array(arr, copy=True), blob
+    return int(rc), out[:n], blob
 
 
 def sge_ckpt_info(blob: bytes):
@@ -254,15 +261,14 @@ def sge_ckpt_info(blob: bytes):
 def sge_resume(ctx, blob: bytes, opts: sge_opts | None = None, check: bool = True):
     """Continue from a checkpoint; returns (rc, rows with the counters so far, next checkpoint or None)."""
     n, _ = sge_ckpt_info(blob)
-    out = (sge_result * max(n, 1))()
+    out, optr = _result_array(n)
     ptr, nbytes = C.c_void_p(), C.c_int64(0)
     rc = load_library().sge_resume(ctx, blob, len(blob), C.byref(opts) if opts is not None else None,
-                                   C.cast(out, C.c_void_p), C.byref(ptr), C.byref(nbytes))
+                                   optr, C.byref(ptr), C.byref(nbytes))
     nxt = _take_blob(ptr, nbytes)
     if check and rc not in _STOPS:
         _check(ctx, rc, "sge_resume")
-    arr = np.ctypeslib.as_array(out)[:n] if n else np.zeros(0)
-    return int(rc), np.array(arr, copy=True), nxt
+    return int(rc), out[:n], nxt
 
 
 def sge_enumerate(ctx, tid: int, pid: int, opts: sge_opts | None = None, check: bool = True):

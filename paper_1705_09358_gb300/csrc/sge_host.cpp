@@ -25,6 +25,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 using namespace sge;
@@ -183,6 +184,7 @@ struct TargetRec {
     int n = 0, dw = 0;
     bool directed = false, any_elab = false;
     long long nnz = 0;
+    TargetView cached{};   // view(), taken once the record is complete
     DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj, hub_slot, hub_bits, hub_list;
     TargetView view() const {
         TargetView v;
@@ -221,6 +223,7 @@ struct PatView {
 };
 
 struct PatternRec {
+    PatternView cached{};   // view(), taken once the record is complete
     int k = 0;
     bool directed = false, any_elab = false;
     std::vector<int32_t> lab, odeg, ideg;
@@ -257,12 +260,13 @@ struct Workspace {
         ctask;
     DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
-    DevBuf mbuf, ckpt, wtrace;
+    DevBuf mbuf, ckpt, wtrace, smask;
+    std::vector<JobDesc> hdesc;   // host job records, reused
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     void release() {
         for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
                           &dent, &deoff, &vchg, &cand, &ctask,
-                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt, &wtrace})
+                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt, &wtrace, &smask})
             b->release();
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -290,8 +294,8 @@ struct sge_ctx {
     int sms = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    std::map<int, std::unique_ptr<TargetRec>> targets;
-    std::map<int, std::unique_ptr<PatternRec>> patterns;
+    std::unordered_map<int, std::unique_ptr<TargetRec>> targets;
+    std::unordered_map<int, std::unique_ptr<PatternRec>> patterns;
     int next_target = 1, next_pattern = 1;
     std::string err;
     std::mutex mu;               // guards targets / patterns / err for the serving thread
@@ -502,7 +506,30 @@ struct Job {
 
 struct PairReq {
     int32_t tid, pid;
+    TargetRec *t = nullptr;    // resolved by prepare_pairs
+    PatternRec *p = nullptr;
 };
+
+// Runs body(begin, end) over [0, n) split across a few host threads when n is
+// large (batches of many thousands of pairs), else inline.
+template <class F>
+void parallel_for(int n, F body) {
+    constexpr int MIN_PER_THREAD = 16384;
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(std::min(8, hw), n / MIN_PER_THREAD);
+    if (nt <= 1) {
+        body(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    const int chunk = (n + nt - 1) / nt;
+    for (int t = 1; t < nt; ++t) {
+        const int b = t * chunk, e = std::min(n, b + chunk);
+        if (b < e) th.emplace_back([&body, b, e] { body(b, e); });
+    }
+    body(0, std::min(n, chunk));
+    for (auto &x : th) x.join();
+}
 
 int pow2_at_least(int x) {
     int p = 1;
@@ -535,7 +562,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     for (int q = 0; q < nj; ++q) {
         Job &J = jobs[q];
         J.pair = idx[q];
-        {
+        J.t = reqs[J.pair].t;
+        J.p = reqs[J.pair].p;
+        if (!J.t || !J.p) {
             std::lock_guard<std::mutex> g(ctx->mu);
             J.t = ctx->targets.at(reqs[J.pair].tid).get();
             J.p = ctx->patterns.at(reqs[J.pair].pid).get();
@@ -568,6 +597,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         kernel = SGE_KERNEL_BITSET;
     }
     const bool need_filt_all = kernel == SGE_KERNEL_BITSET;
+    const double t_jobs = now_ms();
 
     // ---------------------------------------------------------- job tables
     long long filt_words = 0, nverts = 0, nunits = 0;
@@ -579,25 +609,33 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             filt_words += (long long)J.p->k * J.t->dw;
         }
     }
-    std::vector<JobDesc> desc(nj);
+    std::vector<JobDesc> &desc = W.hdesc;   // host copy kept across calls (no fresh pages)
+    desc.resize((size_t)nj);
     CK(W.filt.ensure(std::max<long long>(filt_words, 1) * 8), "alloc filter");
     // per job: 4 counters, then nj match-row counts, then nj byte counters
     CK(W.ctr.ensure((size_t)nj * 6 * sizeof(unsigned long long)), "alloc counters");
     CK(cudaMemsetAsync(W.ctr.p, 0, (size_t)nj * 6 * sizeof(unsigned long long), st), "clear counters");
-    for (int q = 0; q < nj; ++q) {
-        Job &J = jobs[q];
-        JobDesc &D = desc[q];
-        std::memset(&D, 0, sizeof(D));
-        D.t = J.t->view();
-        D.p = J.p->view();
-        D.k = J.p->k;
-        D.flags = (J.algo != SGE_RI ? JOB_RIDS : 0) | (any_elab ? JOB_ELAB : 0) | (directed ? JOB_DIRECTED : 0) |
-                  (J.algo == SGE_RIDS_SI_FC ? JOB_FC : 0);
-        D.ctr = W.ctr.as<unsigned long long>() + 4 * (size_t)q;
-        D.mlen = W.ctr.as<unsigned long long>() + 4 * (size_t)nj + q;
-        D.abytes = W.ctr.as<unsigned long long>() + 5 * (size_t)nj + q;
-        D.filt = J.filt_off >= 0 ? W.filt.as<uint64_t>() + J.filt_off : nullptr;
-    }
+    parallel_for(nj, [&](int q0, int q1) {
+        for (int q = q0; q < q1; ++q) {
+            const Job &J = jobs[q];
+            JobDesc &D = desc[q];
+            D.t = J.t->cached;
+            D.p = J.p->cached;
+            D.pos = nullptr;
+            D.back = nullptr;
+            D.ulist = nullptr;
+            D.mbuf = nullptr;
+            D.mcap = 0;
+            D.k = J.p->k;
+            D.flags = (J.algo != SGE_RI ? JOB_RIDS : 0) | (any_elab ? JOB_ELAB : 0) |
+                      (directed ? JOB_DIRECTED : 0) | (J.algo == SGE_RIDS_SI_FC ? JOB_FC : 0);
+            D.ctr = W.ctr.as<unsigned long long>() + 4 * (size_t)q;
+            D.mlen = W.ctr.as<unsigned long long>() + 4 * (size_t)nj + q;
+            D.abytes = W.ctr.as<unsigned long long>() + 5 * (size_t)nj + q;
+            D.filt = J.filt_off >= 0 ? W.filt.as<uint64_t>() + J.filt_off : nullptr;
+        }
+    });
+    const double t_desc = now_ms();
     // units of the domain kernels: (job, pattern vertex, 64-target word)
     std::vector<int> fjobs;  // jobs with a filter block, in order
     for (int q = 0; q < nj; ++q)
@@ -775,7 +813,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     std::vector<int> task_job, task_vert, task_out;
     std::vector<int> fidx(nj, -1);
     for (int x = 0; x < nf; ++x) fidx[fjobs[x]] = x;
-    std::map<const PatternRec *, std::pair<long long, long long>> ri_tables;
+    std::unordered_map<const PatternRec *, std::pair<long long, long long>> ri_tables;
+    ri_tables.reserve(64);
     long long ulist_len = 0;
     std::vector<PosInfo> pq;
     std::vector<BackEdge> bq;
@@ -814,8 +853,10 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     }
     if (ulist_len > INT32_MAX) return fail(ctx, SGE_ERR_OOM, "unparented candidate lists too large");
     if (trace_on())
-        std::fprintf(stderr, "[sge] jobs %d kernel %d kmax %d nwl %d filt_words %lld domains %.3f ms\n", nj, kernel,
-                     kmax, nwl, filt_words, now_ms() - t_start);
+        std::fprintf(stderr,
+                     "[sge] jobs %d kernel %d kmax %d nwl %d filt_words %lld: jobs %.3f, records %.3f, domains and "
+                     "orders %.3f ms\n",
+                     nj, kernel, kmax, nwl, filt_words, t_jobs - t_start, t_desc - t_jobs, now_ms() - t_desc);
     CK(upload(W.pos, pos, st), "upload positions");
     CK(upload(W.back, back, st), "upload back edges");
     CK(W.ulist.ensure((size_t)std::max<long long>(ulist_len, 1) * 4), "alloc lists");
@@ -835,18 +876,22 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         const long long rows = std::max<long long>(match_cap, 1);
         CK(W.mbuf.ensure((size_t)rows * kmax * 4), "alloc match buffer");
     }
-    for (int q = 0; q < nj; ++q) {
-        JobDesc &D = desc[q];
-        D.pos = W.pos.as<PosInfo>() + pos_off[q];
-        D.back = W.back.as<BackEdge>() + back_off[q];
-        D.ulist = W.ulist.as<int32_t>();
-        if (enumerate) {
-            D.mbuf = W.mbuf.as<int32_t>();
-            D.mcap = match_cap;
+    parallel_for(nj, [&](int q0, int q1) {
+        for (int q = q0; q < q1; ++q) {
+            JobDesc &D = desc[q];
+            D.pos = W.pos.as<PosInfo>() + pos_off[q];
+            D.back = W.back.as<BackEdge>() + back_off[q];
+            D.ulist = W.ulist.as<int32_t>();
+            if (enumerate) {
+                D.mbuf = W.mbuf.as<int32_t>();
+                D.mcap = match_cap;
+            }
         }
-    }
+    });
+    const double t_up = now_ms();
     CK(upload(W.jobs, desc, st), "upload jobs");
     const double t_pre = now_ms();
+    if (trace_on()) std::fprintf(stderr, "[sge] job records uploaded in %.3f ms\n", t_pre - t_up);
 
     // -------------------------------------------------------- split (BFS)
     const int shard_count = o.shard_count > 1 ? o.shard_count : 1;
@@ -914,10 +959,14 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         unsigned *bar = reinterpret_cast<unsigned *>(wtot + wcap);
         long long *res = wtot + wcap + 1;
         int *sstat = reinterpret_cast<int *>(res + 4);
+        constexpr long long SPLIT_MASKS = 1ll << 24;   // 64 MiB of replayed candidate ballots
+        const bool have_masks = W.smask.ensure((size_t)SPLIT_MASKS * 4) == cudaSuccess;
+        if (!have_masks) (void)cudaGetLastError();   // without the buffer the write pass tests again
         const cudaError_t le = launch_split_coop(W.jobs.as<JobDesc>(), F0, W.front[0].as<int32_t>(),
                                                  W.front[1].as<int32_t>(), cap_ints, target, max_levels, wtot,
                                                  wcap, bar, res, sstat, count_ctr, directed ? 1 : 0,
-                                                 serving ? 1 : 0, st);
+                                                 serving ? 1 : 0, have_masks ? W.smask.as<uint32_t>() : nullptr,
+                                                 SPLIT_MASKS, st);
         if (le == cudaSuccess) {
             ++launches;
             long long r4[4] = {0, 0, 0, 0};
@@ -1195,7 +1244,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
 }
 
 // Options with defaults applied, checked, and the pairs split by directedness.
-sge_status prepare_pairs(sge_ctx *ctx, const std::vector<PairReq> &reqs, const sge_opts *opts, sge_opts &o,
+sge_status prepare_pairs(sge_ctx *ctx, std::vector<PairReq> &reqs, const sge_opts *opts, sge_opts &o,
                          std::vector<int> &und, std::vector<int> &dir) {
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
@@ -1212,24 +1261,37 @@ sge_status prepare_pairs(sge_ctx *ctx, const std::vector<PairReq> &reqs, const s
     dir.clear();
     {
         std::lock_guard<std::mutex> g(ctx->mu);
+        int last_tid = 0, last_pid = 0;   // consecutive pairs often repeat an id
+        TargetRec *T = nullptr;
+        PatternRec *P = nullptr;
         for (size_t i = 0; i < reqs.size(); ++i) {
-            auto ti = ctx->targets.find(reqs[i].tid);
-            auto pi = ctx->patterns.find(reqs[i].pid);
-            if (ti == ctx->targets.end() || pi == ctx->patterns.end()) {
+            if (!T || reqs[i].tid != last_tid) {
+                auto ti = ctx->targets.find(reqs[i].tid);
+                T = ti == ctx->targets.end() ? nullptr : ti->second.get();
+                last_tid = reqs[i].tid;
+            }
+            if (!P || reqs[i].pid != last_pid) {
+                auto pi = ctx->patterns.find(reqs[i].pid);
+                P = pi == ctx->patterns.end() ? nullptr : pi->second.get();
+                last_pid = reqs[i].pid;
+            }
+            if (!T || !P) {
                 ctx->err = "unknown target or pattern id";
                 return SGE_ERR_NOT_FOUND;
             }
-            if (ti->second->directed != pi->second->directed) {
+            if (T->directed != P->directed) {
                 ctx->err = "target and pattern disagree on directedness";
                 return SGE_ERR_ARG;
             }
-            (ti->second->directed ? dir : und).push_back((int)i);
+            reqs[i].t = T;
+            reqs[i].p = P;
+            (T->directed ? dir : und).push_back((int)i);
         }
     }
     return SGE_OK;
 }
 
-sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vector<PairReq> &reqs,
+sge_status run_pairs(sge_ctx *ctx, Workspace &W, cudaStream_t st, std::vector<PairReq> &reqs,
                      const sge_opts *opts, sge_result *out, bool enumerate, std::vector<int32_t> *rows,
                      long long cap, bool serving = false) {
     sge_opts o;
@@ -1653,6 +1715,7 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
     if (trace_on()) std::fprintf(stderr, "[sge] target n %d: ingested on the device in %.3f ms\n", n, now_ms() - t_in);
     std::lock_guard<std::mutex> gd(ctx->mu);
     const int id = ctx->next_target++;
+    T->cached = T->view();
     ctx->targets[id] = std::move(T);
     *target_id = id;
     return SGE_OK;
@@ -1698,6 +1761,7 @@ sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *s
     CK(cudaStreamSynchronize(st), "pattern upload");
     std::lock_guard<std::mutex> gd(ctx->mu);
     const int id = ctx->next_pattern++;
+    P->cached = P->view();
     ctx->patterns[id] = std::move(P);
     *pattern_id = id;
     return SGE_OK;

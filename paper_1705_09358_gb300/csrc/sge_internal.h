@@ -190,7 +190,7 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
-                              int blocks_per_sm, cudaStream_t st);
+                              int blocks_per_sm, uint32_t *masks, long long mask_total, cudaStream_t st);
 cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,
                         void *tmp, size_t tmp_bytes, cudaStream_t st);
 size_t scan_tmp_bytes(long long n);

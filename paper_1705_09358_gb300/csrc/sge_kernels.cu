@@ -587,20 +587,29 @@ struct SplitCtl {
     long long *result;          // [4]: final frame count, final buffer (0/1), levels done, last total
     int *status;
     int count_ctr;              // 0 in shards other than 0: levels above the frontier are counted once
+    uint32_t *masks;            // candidate ballots of the count pass, replayed by the write pass
+    long long mask_total;       // masks in the buffer (each warp owns mask_total / warps of them)
 };
 
 // One frame of a split level: count its children (pass 0) or write them from
 // `out` on in candidate order and add its counters (pass 1).  Returns the
 // number of children.
+// The count pass stores each chunk's ballot in the warp's mask buffer (wm,
+// mcap masks, position mp) and the write pass replays it instead of testing
+// the candidates again (frames with at least 16 candidates); leaf frames have
+// no children, so the count pass skips them and only the write pass tests
+// them.  Past mcap masks the write pass tests again.
 template <bool DIR>
 __device__ __forceinline__ long long split_frame(const JobDesc *jobs, const int32_t *fr, int *M, int pass,
-                                                 int32_t *fout, long long out, int stride, int count_ctr) {
+                                                 int32_t *fout, long long out, int stride, int count_ctr,
+                                                 uint32_t *wm, long long mcap, long long &mp) {
     const int lane = threadIdx.x & 31;
     const int j = fr[0], depth = fr[1], rbeg = fr[2], rend = fr[3];
     const JobDesc &J = jobs[j];
+    const bool leaf = depth + 1 == J.k;
+    if (pass == 0 && leaf) return 0;
     for (int t = lane; t < depth; t += 32) M[t] = fr[FRAME_HDR + t];
     __syncwarp();
-    const bool leaf = depth + 1 == J.k;
     const PosInfo P = J.pos[depth];
     const Src src = cand_source(J, P, M);
     const int c_lo = rbeg >= 0 ? rbeg : 0, c_hi = rbeg >= 0 ? min(rend, src.len) : src.len;
@@ -610,15 +619,23 @@ __device__ __forceinline__ long long split_frame(const JobDesc *jobs, const int3
         for (int t = lane; t < depth; t += 32) psum += gterm(J.pos[t].pv, M[t]);
         psum = warp_sum(psum);
     }
+    // short rows are cheaper to test twice than to store and reload
+    const bool masked = !leaf && c_hi - c_lo >= 16;
     for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
         const int idx = c0 + lane;
         bool ok = false;
         int c = -1;
+        const bool replay = pass == 1 && masked && mp < mcap;
         if (idx < c_hi) {
             c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
-            ok = feasible<DIR>(J, P, depth, c, (src.ptr && P.par >= 0) ? src.base + idx : -1, M);
+            if (replay) ok = (wm[mp] >> lane) & 1u;
+            else ok = feasible<DIR>(J, P, depth, c, (src.ptr && P.par >= 0) ? src.base + idx : -1, M);
         }
         const unsigned bal = __ballot_sync(FULL, ok);
+        if (masked) {
+            if (pass == 0 && mp < mcap && lane == 0) wm[mp] = bal;
+            ++mp;
+        }
         const int cnt = __popc(bal);
         if (pass == 1) {
             nodes += cnt;
@@ -661,6 +678,8 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long F = f0, total = 0;
     int cur = 0, level = 0;
+    const long long mcap = S.masks ? S.mask_total / nw : 0;
+    uint32_t *wm = S.masks ? S.masks + w * mcap : nullptr;
     for (; level < S.max_levels; ++level) {
         if (F == 0 || F >= S.target) break;
         const int32_t *fin = cur ? S.buf1 : S.buf0;
@@ -668,9 +687,9 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         const int sin = FRAME_HDR + level, sout = FRAME_HDR + level + 1;   // all frames of a level share a depth
         // each warp owns a contiguous slice of the frontier, so children come out in search order
         const long long lo = F * w / nw, hi = F * (w + 1) / nw;
-        long long mine = 0;
+        long long mine = 0, mp = 0;
         for (long long f = lo; f < hi; ++f)
-            mine += split_frame<DIR>(jobs, fin + f * sin, M, 0, fout, 0, sout, S.count_ctr);
+            mine += split_frame<DIR>(jobs, fin + f * sin, M, 0, fout, 0, sout, S.count_ctr, wm, mcap, mp);
         if (lane == 0) S.wtot[w] = mine;
         grid_barrier(S.bar, S.bar + 1, S.status);
         if (blockIdx.x == 0) {
@@ -694,8 +713,10 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         if (total * sout > S.cap_ints) break;   // the next level does not fit: keep this frontier
         const long long out = *(volatile long long *)(S.wtot + w);
         long long written = 0;
+        mp = 0;
         for (long long f = lo; f < hi; ++f)
-            written += split_frame<DIR>(jobs, fin + f * sin, M, 1, fout, out + written, sout, S.count_ctr);
+            written += split_frame<DIR>(jobs, fin + f * sin, M, 1, fout, out + written, sout, S.count_ctr, wm,
+                                        mcap, mp);
         grid_barrier(S.bar, S.bar + 1, S.status);
         F = total;
         cur ^= 1;
@@ -1847,10 +1868,11 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
-                              int blocks_per_sm, cudaStream_t st) {
+                              int blocks_per_sm, uint32_t *masks, long long mask_total, cudaStream_t st) {
     SplitCtl S;
     S.buf0 = buf0; S.buf1 = buf1; S.cap_ints = cap_ints; S.target = target; S.max_levels = max_levels;
     S.wtot = wtot; S.bar = bar; S.result = result; S.status = status; S.count_ctr = count_ctr;
+    S.masks = masks; S.mask_total = masks ? mask_total : 0;
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
