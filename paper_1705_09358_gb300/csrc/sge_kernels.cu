@@ -1392,12 +1392,16 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 // adjacency bitset and `used` the images M_0..M_{i-1} (rule 1).  Lane l owns
 // words l, l + 32, ... (NWL per lane).
 //
-// Per warp, shared memory holds the used bitset, M, a compact copy of the
-// job's position table, and for every level a list of
-// up to LIST_CAP pending survivors; a level with more survivors keeps its
+// Per warp, registers hold the used-vertex bitset (lane l: words l + 32 w) and
+// shared memory holds M, a compact copy of the job's position table, and for
+// every level a list of up to list_cap(kmax) pending survivors; a level with
+// more survivors keeps its
 // bitset in the warp's slab of global scratch (`SearchCtl::slab`) instead.
 
-constexpr int LIST_CAP = 16;
+// Capacity of a level's survivor list in shared memory: 64 for patterns of up
+// to 32 vertices (measured fastest on the dense workload), 16 beyond so that
+// four blocks of eight warps still fit an SM.  (The length byte reserves 0xff.)
+__host__ __device__ __forceinline__ int list_cap(int kmax) { return kmax <= 32 ? 64 : 16; }
 constexpr uint8_t LIST_SPILLED = 0xff;
 
 struct PosB {
@@ -1409,7 +1413,7 @@ __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl)
     return round16(8 +                                      // the frame's range (for checkpoints)
                    (size_t)kmax * 4 +                       // M
                    (size_t)kmax * sizeof(PosB) +            // position table
-                   (size_t)kmax * LIST_CAP * 2 +            // survivor lists
+                   (size_t)kmax * list_cap(kmax) * 2 +      // survivor lists
                    (size_t)kmax +                           // list lengths
                    (size_t)kmax * (kmax - 1) / 2 + 16);     // back-edge positions
 }
@@ -1427,7 +1431,8 @@ struct BitsJob {
 struct BitsWarp {
     int *M;
     PosB *tab;
-    uint16_t *lst;     // [kmax][LIST_CAP]
+    uint16_t *lst;     // [kmax][lcap]
+    int lcap;          // list_cap(kmax)
     uint8_t *lcnt;     // [kmax]
     uint8_t *tback;
     int *frange;       // [2]: the current frame's candidate range
@@ -1529,14 +1534,14 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
         __syncwarp();
         return 0;
     }
-    if (total <= LIST_CAP) {
+    if (total <= W.lcap) {
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += y;
         }
-        uint16_t *L = W.lst + i * LIST_CAP;
+        uint16_t *L = W.lst + i * W.lcap;
         int o = incl - cnt;
 #pragma unroll
         for (int w = 0; w < NWL; ++w) {
@@ -1567,7 +1572,7 @@ __device__ __forceinline__ int bits_next(const BitsWarp &W, int l) {
     const int c = W.lcnt[l];
     if (c != LIST_SPILLED) {
         if (c == 0) return -1;
-        const int v = W.lst[l * LIST_CAP + c - 1];
+        const int v = W.lst[l * W.lcap + c - 1];
         __syncwarp();
         if (lane == 0) W.lcnt[l] = (uint8_t)(c - 1);
         __syncwarp();
@@ -1598,7 +1603,7 @@ __device__ __forceinline__ void bits_unnext(const BitsWarp &W, int l, int v) {
     const int c = W.lcnt[l];
     __syncwarp();
     if (c != LIST_SPILLED) {
-        if (lane == 0) { W.lst[l * LIST_CAP + c] = (uint16_t)v; W.lcnt[l] = (uint8_t)(c + 1); }
+        if (lane == 0) { W.lst[l * W.lcap + c] = (uint16_t)v; W.lcnt[l] = (uint8_t)(c + 1); }
     } else {
         const int q = v >> 6;
         if (lane == (q & 31)) W.slab[(size_t)l * NWL * 32 + (q >> 5) * 32 + lane] |= 1ull << (v & 63);
@@ -1616,7 +1621,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     W.M = W.frange + 2;
     W.tab = reinterpret_cast<PosB *>(W.M + kmax);
     W.lst = reinterpret_cast<uint16_t *>(W.tab + kmax);
-    W.lcnt = reinterpret_cast<uint8_t *>(W.lst + (size_t)kmax * LIST_CAP);
+    W.lcap = list_cap(kmax);
+    W.lcnt = reinterpret_cast<uint8_t *>(W.lst + (size_t)kmax * W.lcap);
     W.tback = W.lcnt + kmax;
     W.slab = C.slab + ((size_t)blockIdx.x * WARPS_PER_BLOCK + wib) * bits_slab_words_per_warp(kmax, NWL);
     int *M = W.M;
@@ -1771,7 +1777,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     const int c = W.lcnt[l];
                     if (c == 0) continue;
                     if (c != LIST_SPILLED) {
-                        const int vmax = W.lst[l * LIST_CAP + c - 1];
+                        const int vmax = W.lst[l * W.lcap + c - 1];
                         hi = lst ? lower_bound_warp(lst, len, vmax + 1) : vmax + 1;
                     } else {
                         const int vmin = bits_next<NWL>(W, l);
