@@ -40,10 +40,11 @@ constexpr unsigned long long IDLE_GUARD_NS = 60ull * 1000000000ull;   // 60 s id
 constexpr long long RESERVE_SPIN_LIMIT = 1 << 20;   // bounded wait for a queue cell's previous lap
 constexpr int RESERVE_TICKETS = 64;                  // producer tickets tried before keeping the work
 // Idle back-off caps (ns): one warp per block polls for work at short
-// intervals, the others at long ones, so thousands of idle warps do not
-// crowd the queue's lines while the busy warps use them.
-constexpr unsigned IDLE_BACKOFF_FAST = 1024;
-constexpr unsigned IDLE_BACKOFF_SLOW = 32768;
+// intervals, the others at longer ones.  A waiting consumer polls only its own
+// queue cell, so short intervals cost little and hand donated work over fast
+// (measured: 256 ns / 4 us beat 1 us / 32 us by ~2.5% on the dense workload).
+constexpr unsigned IDLE_BACKOFF_FAST = 256;
+constexpr unsigned IDLE_BACKOFF_SLOW = 4096;
 
 __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
