@@ -187,7 +187,8 @@ def _measured_traffic():
     workload, or None when the kernel source has changed since that capture."""
     import hashlib
     try:
-        rec = dict(line.strip().split("=", 1) for line in open(TRAFFIC_FILE) if "=" in line)
+        rec = dict(line.strip().split("=", 1) for line in open(TRAFFIC_FILE)
+                   if "=" in line and not line.startswith("#"))
         with open(KERNEL_SOURCE, "rb") as f:
             src = hashlib.sha256(f.read()).hexdigest()
     except OSError:
