@@ -452,11 +452,14 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
-    world, rank, local = dist_setup()
     if args.impl == "reference":
+        # the oracle runs on the host cores of rank 0 alone; no device, no process group
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
         run_reference(args, world, rank)
-    else:
-        run_ours(args, world, rank, local)
+        return
+    world, rank, local = dist_setup()
+    run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
