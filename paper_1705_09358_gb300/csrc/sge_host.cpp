@@ -698,7 +698,10 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                     ncand += csize[(size_t)g];
                 }
             }
-            const bool cand_mode = ncand > 0 && ncand <= CAND_MAX;
+            // SGE_DOMAIN_WORDS=1 forces the word sweeps (they otherwise serve only lists beyond CAND_MAX)
+            static const bool force_words = std::getenv("SGE_DOMAIN_WORDS") != nullptr &&
+                                            std::getenv("SGE_DOMAIN_WORDS")[0] == '1';
+            const bool cand_mode = !force_words && ncand > 0 && ncand <= CAND_MAX;
             if (cand_mode) {
                 std::vector<int> tj, tv, to;
                 for (long long g = 0; g < nverts; ++g)

@@ -172,3 +172,34 @@ def test_cl100k_rids_variants_sample():
         for i, p in enumerate(pats):
             want = oracle.run(ot, p, algo)
             assert counters(rows[i]) == counters(want), (algo, i)
+
+
+def test_domain_word_sweeps_match_candidate_sweeps():
+    """Arc consistency runs over candidate lists, or over 64-target words when the lists
+    would be too large; both must reach the same fixpoint.  The word sweeps are forced
+    (SGE_DOMAIN_WORDS=1, read once per process) in a child process on cl10k."""
+    import json
+    import os
+    import subprocess
+    import sys
+    g = golden("cl10k")
+    code = (
+        "import json, sys\n"
+        "sys.path.insert(0, 'tests'); sys.path.insert(0, '.')\n"
+        "from gen import configs\n"
+        "import paper_1705_09358_gb300 as sge\n"
+        "w = configs.cl10k()\n"
+        "with sge.Context(0) as E:\n"
+        "    tid = E.load_target(w.targets[0])\n"
+        "    pids = [E.load_pattern(p) for p in w.patterns]\n"
+        "    rc, rows = E.count_batch([tid] * len(pids), pids, algo=3)\n"
+        "    print(json.dumps([[int(r[k]) for k in ('matches', 'states', 'nodes', 'hash')] for r in rows]))\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SGE_DOMAIN_WORDS="1")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    got = json.loads(out.stdout.strip().splitlines()[-1])
+    want = [list(golden_counters(ent["algos"]["3"])) for ent in g["patterns"]]
+    assert got == want
