@@ -1528,13 +1528,9 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
         }
         return total;
     }
-    // pending survivors: a short list in shared memory, else the bitset in the slab
-    if (total == 0) {
-        __syncwarp();
-        if (lane == 0) W.lcnt[i] = 0;
-        __syncwarp();
-        return 0;
-    }
+    // pending survivors: a short list in shared memory, else the bitset in the slab.
+    // With none, level i's list is left as it was: the caller does not descend to it.
+    if (total == 0) return 0;
     if (total <= W.lcap) {
         int incl = cnt;
 #pragma unroll
@@ -1698,8 +1694,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         if (!fr.counted) nd += c0;
         if (leaf0) {
             mt += c0;
-        } else {
-            int lvl = d0;
+        } else if (c0 > 0) {
+            // Levels d0..lvl hold pending survivors; `cur` is M[lvl] (-1 before the
+            // level's first choice).  An expansion that finds no survivors does not
+            // descend, so a level's list is read only after an expansion filled it.
+            int lvl = d0, cur = -1;
             for (;;) {
                 if (((++iter) & 63) == 0 && time_to_check(last_check)) {
                     if (C.budget > 0) {
@@ -1732,27 +1731,28 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         donation_done(C);
                     }
                 }
-                const int prev = M[lvl];
-                if (prev >= 0) used_flip<NWL>(used, prev);      // leave the previous choice at this level
+                if (cur >= 0) used_flip<NWL>(used, cur);        // leave the previous choice at this level
                 const int v = bits_next<NWL>(W, lvl);
                 if (v < 0) {
-                    if (lane == 0) M[lvl] = -1;
-                    __syncwarp();
                     if (lvl == d0) break;
                     --lvl;
+                    cur = M[lvl];
                     continue;
                 }
                 used_flip<NWL>(used, v);
                 if (lane == 0) M[lvl] = v;
                 __syncwarp();
-                if (lvl + 1 == k - 1) {
-                    const int c = bits_expand<NWL>(B, J, W, used, lvl + 1, true, st, hs, ab);
-                    nd += c; mt += c;
-                } else {
-                    nd += bits_expand<NWL>(B, J, W, used, lvl + 1, false, st, hs, ab);
+                const bool leaf = lvl + 1 == k - 1;
+                const int c = bits_expand<NWL>(B, J, W, used, lvl + 1, leaf, st, hs, ab);
+                nd += c;
+                if (leaf) {
+                    mt += c;
+                    cur = v;
+                } else if (c > 0) {
                     ++lvl;
-                    if (lane == 0) M[lvl] = -1;
-                    __syncwarp();
+                    cur = -1;
+                } else {
+                    cur = v;
                 }
             }
             if (stopped && C.ckpt != nullptr) {
