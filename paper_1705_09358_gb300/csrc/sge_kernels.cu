@@ -1405,15 +1405,16 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 __host__ __device__ __forceinline__ int list_cap(int kmax) { return kmax <= 32 ? 64 : 16; }
 constexpr uint8_t LIST_SPILLED = 0xff;
 
-struct PosB {
+struct __align__(16) PosB {
     int16_t pv, par, bb, bc;  // pattern vertex, parent position, back-edge range
     int32_t ucnt;             // raw candidates of an unparented position
+    int32_t abytes;           // algorithmic bytes of one expansion: rows ANDed x dw x 8
 };
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
-    return round16(8 +                                      // the frame's range (for checkpoints)
+    return round16((size_t)kmax * sizeof(PosB) +            // position table (16-byte aligned)
+                   8 +                                      // the frame's range (for checkpoints)
                    (size_t)kmax * 4 +                       // M
-                   (size_t)kmax * sizeof(PosB) +            // position table
                    (size_t)kmax * list_cap(kmax) * 2 +      // survivor lists
                    (size_t)kmax +                           // list lengths
                    (size_t)kmax * (kmax - 1) / 2 + 16);     // back-edge positions
@@ -1445,18 +1446,26 @@ __device__ __forceinline__ void used_flip(uint64_t (&used)[NWL], int v) {
     // lane (q mod 32) holds word q of the used bitset in register used[q / 32]
     const int q = v >> 6;
     if ((threadIdx.x & 31) == (q & 31)) {
+        const uint64_t bit = 1ull << (v & 63);
+        if (NWL == 1) {
+            used[0] ^= bit;   // v < 64 * 32: q < 32
+        } else {
 #pragma unroll
-        for (int w = 0; w < NWL; ++w)
-            if (w == (q >> 5)) used[w] ^= 1ull << (v & 63);
+            for (int w = 0; w < NWL; ++w)
+                if (w == (q >> 5)) used[w] ^= bit;
+        }
     }
 }
 
 // Expand position i: compute S_i, count its survivors (the accepted nodes),
 // and either hash them as matches (leaf) or keep them as pending survivors.
+// `st` and `ab` are 32-bit: one expansion adds at most n_t <= 8192 states and
+// (k_max + 1) x 128 x 8 bytes, and the caller folds them into 64-bit totals
+// every 64 expansions.
 template <int NWL, bool RANGE = false>
 __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W,
                                            const uint64_t (&used)[NWL], int i, bool leaf,
-                                           unsigned long long &st, unsigned long long &hs, unsigned long long &ab,
+                                           unsigned &st, unsigned long long &hs, unsigned &ab,
                                            int vlo = 0, int vhi = 0x7fffffff, bool count_len = true) {
     const int lane = threadIdx.x & 31;
     const PosB p = W.tab[i];
@@ -1489,8 +1498,8 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
             if (q < dw) s[w] &= __ldg(X + q);
         }
     }
-    if (count_len) st += (unsigned long long)len;
-    ab += (unsigned long long)((p.par >= 0 ? 2 : 1) + p.bc) * (unsigned long long)dw * 8ull;
+    if (count_len) st += (unsigned)len;
+    ab += (unsigned)p.abytes;
     int cnt = 0;
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
@@ -1614,10 +1623,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
     BitsWarp W;
-    W.frange = reinterpret_cast<int *>(base);
+    W.tab = reinterpret_cast<PosB *>(base);
+    W.frange = reinterpret_cast<int *>(W.tab + kmax);
     W.M = W.frange + 2;
-    W.tab = reinterpret_cast<PosB *>(W.M + kmax);
-    W.lst = reinterpret_cast<uint16_t *>(W.tab + kmax);
+    W.lst = reinterpret_cast<uint16_t *>(W.M + kmax);
     W.lcap = list_cap(kmax);
     W.lcnt = reinterpret_cast<uint8_t *>(W.lst + (size_t)kmax * W.lcap);
     W.tback = W.lcnt + kmax;
@@ -1627,7 +1636,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
 
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
-    long long iter = 0, last_don_iter = 0;
+    unsigned iter = 0, last_don_iter = 0;
     unsigned long long last_check = 0, last_don_ns = 0, last_cancel = 0;
     int cur_job = -1;
     BitsJob B;
@@ -1644,6 +1653,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                 PosB q;
                 q.pv = (int16_t)P.pv; q.par = (int16_t)P.par; q.bb = (int16_t)P.bbeg; q.bc = (int16_t)P.bcnt;
                 q.ucnt = (J.flags & JOB_RIDS) ? P.ucnt : J.t.n;   // RI: all of V_t
+                q.abytes = ((P.par >= 0 ? 2 : 1) + P.bcnt) * J.t.dw * 8;
                 W.tab[t] = q;
             }
             __syncwarp();
@@ -1652,7 +1662,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             __syncwarp();
         }
         const int k = B.k, d0 = fr.depth;
-        unsigned long long st = 0, nd = 0, mt = 0, hs = 0, ab = 0;
+        unsigned long long st = 0, nd = 0, mt = 0, hs = 0, ab = 0;   // the frame's totals
+        unsigned st32 = 0, nd32 = 0, mt32 = 0, ab32 = 0;               // since the last fold
         {
 #pragma unroll
             for (int w = 0; w < NWL; ++w) used[w] = 0ull;
@@ -1689,8 +1700,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         if (lane == 0) { W.frange[0] = fr.beg; W.frange[1] = fr.end; }   // read back only by a checkpoint
         const bool count_len = fr.beg <= 0 && !fr.counted;
         const bool leaf0 = d0 == k - 1;
-        const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, used, d0, leaf0, st, hs, ab, vlo, vhi, count_len)
-                                   : bits_expand<NWL>(B, J, W, used, d0, leaf0, st, hs, ab);
+        const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, used, d0, leaf0, st32, hs, ab32, vlo, vhi, count_len)
+                                   : bits_expand<NWL>(B, J, W, used, d0, leaf0, st32, hs, ab32);
         if (!fr.counted) nd += c0;
         if (leaf0) {
             mt += c0;
@@ -1700,13 +1711,17 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             // descend, so a level's list is read only after an expansion filled it.
             int lvl = d0, cur = -1;
             for (;;) {
-                if (((++iter) & 63) == 0 && time_to_check(last_check)) {
+                if (((++iter) & 63) == 0) {
+                    st += st32; nd += nd32; mt += mt32; ab += ab32;
+                    st32 = nd32 = mt32 = ab32 = 0;
+                }
+                if ((iter & 63) == 0 && time_to_check(last_check)) {
                     if (C.budget > 0) {
                         if (lane == 0) atomicAdd(J.ctr + 1, st);
                         st = 0;
                     }
                     if (must_stop(C, J, st, deadline, last_check, last_cancel)) { stopped = true; break; }
-                    if ((iter - last_don_iter >= C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
+                    if ((iter - last_don_iter >= (unsigned)C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
                         donation_claim(C)) {
                         // donate up to `gran` pending survivors of the shallowest level that has some
                         last_don_iter = iter;
@@ -1743,10 +1758,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                 if (lane == 0) M[lvl] = v;
                 __syncwarp();
                 const bool leaf = lvl + 1 == k - 1;
-                const int c = bits_expand<NWL>(B, J, W, used, lvl + 1, leaf, st, hs, ab);
-                nd += c;
+                const int c = bits_expand<NWL>(B, J, W, used, lvl + 1, leaf, st32, hs, ab32);
+                nd32 += c;
                 if (leaf) {
-                    mt += c;
+                    mt32 += c;
                     cur = v;
                 } else if (c > 0) {
                     ++lvl;
@@ -1789,6 +1804,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                 }
             }
         }
+        st += st32; nd += nd32; mt += mt32; ab += ab32;
         hs = warp_sum(hs);
         if (lane == 0) {
             atomicAdd(J.ctr + 0, mt);
