@@ -1489,7 +1489,7 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
         }
         len = __ldg(B.vld + a).y;
     }
-#pragma unroll 4
+#pragma unroll 2
     for (int b = 0; b < p.bc; ++b) {
         const uint64_t *X = B.adj + (size_t)M[W.tback[p.bb + b]] * dw;
 #pragma unroll
