@@ -151,7 +151,10 @@ sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *s
                             const int32_t *vlabel, const int32_t *elabel, int32_t directed,
                             int32_t *pattern_id);
 
-/* Release a loaded graph's device memory.  NOT_FOUND for an unknown id. */
+/* Release a loaded graph.  Waits until the device is idle, then keeps the
+ * graph's device blocks in the context (up to 1 GiB) for later loads, which
+ * take them instead of allocating; sge_destroy frees them.  NOT_FOUND for an
+ * unknown id. */
 sge_status sge_unload_target(sge_ctx *ctx, int32_t target_id);
 sge_status sge_unload_pattern(sge_ctx *ctx, int32_t pattern_id);
 

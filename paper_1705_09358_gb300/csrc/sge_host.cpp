@@ -59,22 +59,79 @@ double now_ms() {
 }
 
 // ------------------------------------------------------------ device buffers
+// Device blocks of unloaded graphs, kept by the context for the next load: a
+// load then needs no cudaMalloc and an unload no cudaFree (each cudaFree
+// synchronises the device).  Blocks are handed back only after the device is
+// idle (sge_unload_*) or when only the context's own stream used them (a
+// failed load), so a block is never reused while a kernel still reads it.
+struct BlockCache {
+    static constexpr size_t LIMIT = size_t(1) << 30;   // cached bytes kept at most
+    std::mutex mu;
+    std::multimap<size_t, void *> blocks;              // capacity -> block
+    size_t bytes = 0;
+    // A cached block of at least `want` bytes and at most about twice that.
+    void *take(size_t want, size_t *cap) {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = blocks.lower_bound(want);
+        if (it == blocks.end() || it->first > 2 * want + 4096) return nullptr;
+        void *q = it->second;
+        *cap = it->first;
+        bytes -= it->first;
+        blocks.erase(it);
+        return q;
+    }
+    void give(void *q, size_t cap) {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            if (bytes + cap <= LIMIT) {
+                blocks.emplace(cap, q);
+                bytes += cap;
+                return;
+            }
+        }
+        cudaFree(q);
+    }
+    // Free every cached block; returns whether there were any.
+    bool clear() {
+        std::lock_guard<std::mutex> g(mu);
+        const bool had = !blocks.empty();
+        for (auto &kv : blocks) cudaFree(kv.second);
+        blocks.clear();
+        bytes = 0;
+        return had;
+    }
+};
+
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    BlockCache *cache = nullptr;   // where released blocks go (null: cudaFree)
     cudaError_t ensure(size_t bytes) {
         if (bytes <= cap && p) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
+        release();
         size_t nb = bytes < 256 ? 256 : bytes;
+        if (cache) {
+            size_t c = 0;
+            if (void *q = cache->take(nb, &c)) {
+                p = q;
+                cap = c;
+                return cudaSuccess;
+            }
+        }
         cudaError_t e = cudaMalloc(&p, nb);
+        if (e == cudaErrorMemoryAllocation && cache && cache->clear()) {
+            cudaGetLastError();   // the failed attempt must not surface at a later launch check
+            e = cudaMalloc(&p, nb);
+        }
         if (e != cudaSuccess) { p = nullptr; return e; }
         cap = nb;
         return cudaSuccess;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (cache) cache->give(p, cap);
+            else cudaFree(p);
+        }
         p = nullptr;
         cap = 0;
     }
@@ -204,11 +261,17 @@ struct TargetRec {
         v.hub_bits = hub_bits.p ? hub_bits.as<uint64_t>() : nullptr;
         return v;
     }
+    void use_cache(BlockCache *c) {
+        for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
+                          &hub_list})
+            b->cache = c;
+    }
     void release() {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
                           &hub_list})
             b->release();
     }
+    ~TargetRec() { release(); }
 };
 
 // The host-side facts about a pattern that the ordering and the position
@@ -249,9 +312,13 @@ struct PatternRec {
         v.ielab = directed ? dielab.as<int32_t>() : v.elab;
         return v;
     }
+    void use_cache(BlockCache *c) {
+        for (DevBuf *b : {&dlab, &dodeg, &dideg, &drow, &dcol, &delab, &dirow, &dicol, &dielab}) b->cache = c;
+    }
     void release() {
         for (DevBuf *b : {&dlab, &dodeg, &dideg, &drow, &dcol, &delab, &dirow, &dicol, &dielab}) b->release();
     }
+    ~PatternRec() { release(); }
 };
 
 // Scratch of one launch sequence (the serving scheduler has one per slot).
@@ -294,6 +361,7 @@ struct sge_ctx {
     int sms = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    BlockCache cache;            // device blocks of unloaded graphs (declared before the graphs)
     std::unordered_map<int, std::unique_ptr<TargetRec>> targets;
     std::unordered_map<int, std::unique_ptr<PatternRec>> patterns;
     int next_target = 1, next_pattern = 1;
@@ -1579,6 +1647,7 @@ void sge_destroy(sge_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->targets) kv.second->release();
     for (auto &kv : ctx->patterns) kv.second->release();
+    ctx->cache.clear();
     ctx->ws.release();
     ctx->ing.release();
     if (ctx->cancel_host) cudaFreeHost(ctx->cancel_host);
@@ -1600,6 +1669,7 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
     std::lock_guard<std::mutex> ig(ctx->ingest_mu);
     IngestWs &I = ctx->ing;
     auto T = std::make_unique<TargetRec>();
+    T->use_cache(&ctx->cache);
     T->n = n;
     T->directed = directed != 0;
     T->dw = std::max(1, (n + 63) / 64);
@@ -1734,6 +1804,7 @@ sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *s
     cudaSetDevice(ctx->device);
     cudaStream_t st = ctx->stream;
     auto P = std::make_unique<PatternRec>();
+    P->use_cache(&ctx->cache);
     P->k = n;
     P->directed = g.directed;
     P->any_elab = g.any_elab;
@@ -1775,7 +1846,9 @@ sge_status sge_unload_target(sge_ctx *ctx, int32_t target_id) {
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->targets.find(target_id);
     if (it == ctx->targets.end()) return SGE_ERR_NOT_FOUND;
-    cudaStreamSynchronize(ctx->stream);
+    // the blocks go back to the context's cache: wait until no kernel on any stream reads them
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
     it->second->release();
     ctx->targets.erase(it);
     return SGE_OK;
@@ -1786,7 +1859,9 @@ sge_status sge_unload_pattern(sge_ctx *ctx, int32_t pattern_id) {
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->patterns.find(pattern_id);
     if (it == ctx->patterns.end()) return SGE_ERR_NOT_FOUND;
-    cudaStreamSynchronize(ctx->stream);
+    // the blocks go back to the context's cache: wait until no kernel on any stream reads them
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
     it->second->release();
     ctx->patterns.erase(it);
     return SGE_OK;

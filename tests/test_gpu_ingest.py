@@ -129,3 +129,20 @@ def test_empty_and_edgeless_targets():
     _count_both(Graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(5, np.int32)),
                 Graph(2, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(2, np.int32)))
     _count_both(complete(7), star(3))
+
+
+def test_unloaded_blocks_are_reused_without_stale_data():
+    # Unloaded graphs leave their device blocks in the context for later loads.  Load,
+    # count and unload targets and patterns of changing sizes in turn, so that each load
+    # takes blocks still holding an earlier graph's rows, adjacency bits and labels; every
+    # count must still be the oracle's.
+    rng = np.random.default_rng(11)
+    for n, p_edge in [(300, 0.2), (260, 0.25), (150, 0.3), (300, 0.15), (290, 0.2)]:
+        iu = np.triu_indices(n, 1)
+        keep = rng.random(len(iu[0])) < p_edge
+        t = Graph(n, iu[0][keep].astype(np.int32), iu[1][keep].astype(np.int32),
+                  rng.integers(0, 2, size=n).astype(np.int32))
+        k = int(rng.integers(3, 5))   # cycles of 3 or 4: a few million states for the oracle
+        p = edges_graph(k, [(i, i + 1) for i in range(k - 1)] + [(0, k - 1)],
+                        labels=[int(x) for x in rng.integers(0, 2, size=k)])
+        _count_both(t, p)
