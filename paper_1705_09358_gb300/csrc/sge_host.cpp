@@ -293,7 +293,10 @@ struct PatternRec {
     std::vector<int> amat;                 // k x k arc labels, NO_ARC if absent
     std::vector<uint64_t> nb;              // undirected neighbourhood bitsets (2 words per vertex)
     std::vector<int> ri_mu, ri_par;        // cached RI ordering
-    DevBuf dlab, dodeg, dideg, drow, dcol, delab, dirow, dicol, dielab;
+    // the device arrays, packed into one block (one upload per load) at these
+    // int32 offsets, each a multiple of 4 (16-byte aligned)
+    DevBuf dall;
+    size_t o_lab = 0, o_odeg = 0, o_ideg = 0, o_row = 0, o_col = 0, o_elab = 0, o_irow = 0, o_icol = 0, o_ielab = 0;
     PatView core() const {
         return PatView{k, directed, lab.data(), odeg.data(), ideg.data(), amat.data(), nb.data()};
     }
@@ -301,23 +304,22 @@ struct PatternRec {
         PatternView v;
         v.k = k;
         v.pad = 0;
-        v.lab = dlab.as<int32_t>();
-        v.odeg = dodeg.as<int32_t>();
-        v.ideg = directed ? dideg.as<int32_t>() : dodeg.as<int32_t>();
-        v.rowptr = drow.as<int32_t>();
-        v.col = dcol.as<int32_t>();
-        v.elab = delab.as<int32_t>();
-        v.irowptr = directed ? dirow.as<int32_t>() : v.rowptr;
-        v.icol = directed ? dicol.as<int32_t>() : v.col;
-        v.ielab = directed ? dielab.as<int32_t>() : v.elab;
+        const int32_t *b = dall.as<int32_t>();
+        v.lab = b + o_lab;
+        v.odeg = b + o_odeg;
+        v.ideg = directed ? b + o_ideg : v.odeg;
+        v.rowptr = b + o_row;
+        v.col = b + o_col;
+        v.elab = b + o_elab;
+        v.irowptr = directed ? b + o_irow : v.rowptr;
+        v.icol = directed ? b + o_icol : v.col;
+        v.ielab = directed ? b + o_ielab : v.elab;
         return v;
     }
     void use_cache(BlockCache *c) {
-        for (DevBuf *b : {&dlab, &dodeg, &dideg, &drow, &dcol, &delab, &dirow, &dicol, &dielab}) b->cache = c;
+        dall.cache = c;
     }
-    void release() {
-        for (DevBuf *b : {&dlab, &dodeg, &dideg, &drow, &dcol, &delab, &dirow, &dicol, &dielab}) b->release();
-    }
+    void release() { dall.release(); }
     ~PatternRec() { release(); }
 };
 
@@ -1821,17 +1823,25 @@ sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *s
             P->nb[2 * w + (v >> 6)] |= 1ull << (v & 63);
         }
     gcf_order(*P, SGE_RI, nullptr, P->ri_mu, P->ri_par);
-    CK(upload(P->dlab, g.vlab, st), "upload pattern labels");
-    CK(upload(P->dodeg, g.odeg, st), "upload pattern degrees");
-    CK(upload(P->drow, g.out.ptr, st), "upload pattern rows");
-    CK(upload(P->dcol, g.out.col, st), "upload pattern cols");
-    CK(upload(P->delab, g.out.lab, st), "upload pattern edge labels");
+    std::vector<int32_t> img;   // the host image of P->dall
+    auto put = [&img](const std::vector<int32_t> &v) {
+        const size_t at = img.size();
+        img.insert(img.end(), v.begin(), v.end());
+        img.resize((img.size() + 3) & ~size_t(3), 0);
+        return at;
+    };
+    P->o_lab = put(g.vlab);
+    P->o_odeg = put(g.odeg);
+    P->o_row = put(g.out.ptr);
+    P->o_col = put(g.out.col);
+    P->o_elab = put(g.out.lab);
     if (g.directed) {
-        CK(upload(P->dideg, g.ideg, st), "upload pattern in-degrees");
-        CK(upload(P->dirow, g.in.ptr, st), "upload pattern in-rows");
-        CK(upload(P->dicol, g.in.col, st), "upload pattern in-cols");
-        CK(upload(P->dielab, g.in.lab, st), "upload pattern in-labels");
+        P->o_ideg = put(g.ideg);
+        P->o_irow = put(g.in.ptr);
+        P->o_icol = put(g.in.col);
+        P->o_ielab = put(g.in.lab);
     }
+    CK(upload(P->dall, img, st), "upload pattern");
     CK(cudaStreamSynchronize(st), "pattern upload");
     std::lock_guard<std::mutex> gd(ctx->mu);
     const int id = ctx->next_pattern++;
