@@ -20,6 +20,7 @@ the workload (weak scaling); ranks exchange only the timing maximum.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -50,26 +51,41 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi samples of the SM clock, its maximum and the throttle reasons, kept
+    for the timed region only: each sample carries nvidia-smi's timestamp, compared
+    with the host clock at the region's start and end (same host, local time)."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # let the sampler write its first line before the timed region starts (2 s at most)
+            limit = time.time() + 2.0
+            while time.time() < limit and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
+
+    def start(self):
+        self.t0 = datetime.datetime.now()
+
+    def stop(self):
+        self.t1 = datetime.datetime.now()
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -80,27 +96,37 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self) -> dict:
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []   # (time or None, sm MHz, max MHz, active reasons)
         try:
             with open(self.path) as f:
                 for line in f:
                     parts = [x.strip() for x in line.split(",")]
-                    if len(parts) < 7:
+                    if len(parts) < 8:
                         continue
                     try:
-                        sm.append(float(parts[0]))
-                        mx.append(float(parts[1]))
+                        sm, mx = float(parts[1]), float(parts[2])
                     except ValueError:
                         continue
-                    for nm, v in zip(names, parts[3:7]):
-                        if v.lower() == "active":
-                            reasons.add(nm)
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                    except ValueError:
+                        ts = None
+                    act = {nm for nm, v in zip(self.REASONS, parts[4:8]) if v.lower() == "active"}
+                    rows.append((ts, sm, mx, act))
             os.unlink(self.path)
         except Exception:
             pass
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        window = "whole run"
+        if self.t0 is not None and self.t1 is not None:
+            pad = datetime.timedelta(milliseconds=50)
+            inside = [r for r in rows if r[0] is not None and self.t0 - pad <= r[0] <= self.t1 + pad]
+            if inside:
+                rows, window = inside, "timed region"
+        sm = [r[1] for r in rows]
+        reasons = set().union(*[r[3] for r in rows]) if rows else set()
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+                "samples": len(rows), "window": window, "reasons": sorted(reasons)}
 
 
 def dist_setup():
@@ -226,6 +252,7 @@ def run_ours(args, world, rank, local):
     kernel_ms = 0.0
     kernel_launches = 0
     with Clocks(local) as clk:
+        clk.start()
         with torch.cuda.stream(stream):
             for i in range(args.steps):
                 flush.zero_()                       # evict L2 between timed steps
@@ -239,6 +266,7 @@ def run_ours(args, world, rank, local):
                 kernel_ms += float(rows["search_kernel_ms"][0])
                 kernel_launches += 1
         barrier(world)
+        clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1000.0
     total_s = max_over_ranks(total_s, world)
@@ -299,8 +327,6 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline"] = {"value": smp["states"] / smp["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "the oracle (one thread) on all 5 patterns, each stopped after 2e8 states; "
                                           f"{smp['states']} states in {smp['seconds']:.1f} s"}
-    with Clocks(local) as _:
-        pass
     line["clocks"] = clk.summary()
     E.close()
     if rank == 0:
@@ -441,7 +467,7 @@ def run_ablation(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the CPU baseline and batched comparison")

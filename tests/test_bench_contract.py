@@ -41,3 +41,46 @@ def test_reference_arm_other_ranks_print_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_clock_samples_are_kept_for_the_timed_region_only():
+    import datetime
+    import tempfile
+    sys.path.insert(0, ROOT)
+    import bench
+    t0 = datetime.datetime(2026, 1, 2, 3, 4, 5, 0)
+    lines = []
+    for i in range(20):   # one sample every 100 ms from t0 - 0.5 s
+        ts = t0 + datetime.timedelta(milliseconds=100 * i - 500)
+        idle = i < 5 or i >= 15
+        sm = 1000 if idle else 2070
+        thermal = "Active" if i == 18 else "Not Active"
+        power = "Active" if i == 9 else "Not Active"
+        lines.append(f"{ts.strftime('%Y/%m/%d %H:%M:%S.%f')[:-3]}, {sm}, 2070, 0x0, Not Active, {thermal}, "
+                     f"Not Active, {power}")
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    c = bench.Clocks(0)
+    c.path = path
+    c.t0 = t0
+    c.t1 = t0 + datetime.timedelta(milliseconds=900)
+    s = c.summary()
+    # samples 5..14 lie in [t0, t0 + 0.9 s] (50 ms margin): clocks under load, and only their reasons
+    assert s["window"] == "timed region" and s["samples"] == 10
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_samples_without_a_window_use_the_whole_run():
+    import tempfile
+    sys.path.insert(0, ROOT)
+    import bench
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("not a time, 1800, 2070, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                "garbage line\n")
+    c = bench.Clocks(0)
+    c.path = path
+    s = c.summary()
+    assert s["window"] == "whole run" and s["samples"] == 1 and s["sm_mhz"] == 1800 and s["reasons"] == []
