@@ -208,9 +208,10 @@ KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_
                              "sge_kernels.cu")
 
 
-def _measured_traffic():
-    """DRAM bytes (read + write) per search-kernel launch from the last ncu capture of this
-    workload, or None when the kernel source has changed since that capture."""
+def _measured_record() -> dict:
+    """Per search-kernel launch, from the last ncu capture of this workload: DRAM bytes
+    (read + write) and warp instructions executed; empty when the kernel source has
+    changed since that capture."""
     import hashlib
     try:
         rec = dict(line.strip().split("=", 1) for line in open(TRAFFIC_FILE)
@@ -218,10 +219,33 @@ def _measured_traffic():
         with open(KERNEL_SOURCE, "rb") as f:
             src = hashlib.sha256(f.read()).hexdigest()
     except OSError:
-        return None
+        return {}
     if rec.get("kernel_source_sha256") != src:
+        return {}
+    return rec
+
+
+def _measured_traffic():
+    rec = _measured_record()
+    return int(rec["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in rec else None
+
+
+# Instruction-issue ceiling of a GB300: 152 SMs x 4 warp schedulers, each issuing at most one
+# warp instruction per cycle, at the maximum SM clock of 2070 MHz.
+ISSUE_PEAK = 152 * 4 * 2070e6
+
+
+def issue_roofline(kernel_s_per_launch: float) -> dict | None:
+    """The search kernel against the instruction-issue ceiling: warp instructions per launch
+    (ncu count of the current kernel source) / the live CUDA-event time per launch."""
+    rec = _measured_record()
+    if "warp_instructions_per_launch" not in rec or kernel_s_per_launch <= 0:
         return None
-    return int(rec["dram_bytes_per_launch"])
+    inst = int(rec["warp_instructions_per_launch"])
+    achieved = inst / kernel_s_per_launch
+    return {"bound": "issue", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp instructions/s",
+            "frac": achieved / ISSUE_PEAK, "instructions_per_launch": inst,
+            "peak_kind": "152 SMs x 4 schedulers x 1 instruction/cycle x 2070 MHz"}
 
 
 def run_ours(args, world, rank, local):
@@ -319,7 +343,8 @@ def run_ours(args, world, rank, local):
                        "parallelism": f"replicas x{world}"},
             "matches_per_sec": world * matches / total_s,
             "states_per_step": states // args.steps, "matches_per_step": matches // args.steps,
-            "gpu_launches": launches, "roofline": roofline, "e2e": e2e}
+            "gpu_launches": launches, "roofline": roofline,
+            "issue_roofline": issue_roofline(kernel_ms / kernel_launches / 1000.0), "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_extras:
         line["batched_vs_per_query"] = batched_vs_per_query(E, args)
         line["serving"] = serving_latency(E)

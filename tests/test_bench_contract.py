@@ -84,3 +84,17 @@ def test_clock_samples_without_a_window_use_the_whole_run():
     c.path = path
     s = c.summary()
     assert s["window"] == "whole run" and s["samples"] == 1 and s["sm_mhz"] == 1800 and s["reasons"] == []
+
+
+def test_issue_roofline_follows_the_capture_record():
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = bench._measured_record()
+    r = bench.issue_roofline(5e-3)
+    if not rec:   # kernel source changed since the last capture: nothing is claimed
+        assert r is None and bench._measured_traffic() is None
+        return
+    assert r["bound"] == "issue" and r["peak"] == 152 * 4 * 2070e6
+    assert r["instructions_per_launch"] == int(rec["warp_instructions_per_launch"])
+    assert abs(r["frac"] - r["instructions_per_launch"] / 5e-3 / r["peak"]) < 1e-12
+    assert bench._measured_traffic() == int(rec["dram_bytes_per_launch"])
