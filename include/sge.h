@@ -259,15 +259,24 @@ sge_status sge_serve_drain(sge_ctx *ctx);
  * target too large for that array (about 1.9 million vertices; fewer if
  * the pattern has edge labels and the target has none) is rejected with
  * SGE_ERR_ARG before any device work.  The first call on each device looks
- * up that device's copy of the array; make it before capturing a stream.
- * All calls share the one array, and each call clears the parts that must
- * start at zero, so calls must not overlap on the GPU: calls that run at
- * the same time (on different streams or host threads) race and corrupt
- * each other's results.
+ * up that device's copy of the array (cudaGetSymbolAddress, with that device
+ * current), so that first call should come before any stream capture begins.
+ * All calls share the one array, which keeps the last call's contents; each
+ * call clears the parts that must start at zero, so calls must not overlap
+ * on the GPU: calls that run at the same time (on different streams or host
+ * threads) race and corrupt each other's results.
  *
- * Returns SGE_OK, SGE_ERR_ARG (bad arguments or sizes), SGE_ERR_CUDA, or
- * SGE_ERR_TIMEOUT (out holds partial counters).  The caller's CSR is not
- * validated on the device; ids out of range are undefined behaviour. */
+ * Every device access of the call, including the read of d_rowptr[n] that a
+ * labelled pattern on an unlabelled target needs, is ordered on cuda_stream,
+ * after whatever the caller queued there before.  The pattern's host-side
+ * tables (about 200 KB at 128 vertices) go to one host heap block freed
+ * before return, so the call needs only a few KB of the calling thread's
+ * stack.
+ *
+ * Returns SGE_OK, SGE_ERR_ARG (bad arguments or sizes), SGE_ERR_OOM (the
+ * host block could not be allocated), SGE_ERR_CUDA, or SGE_ERR_TIMEOUT (out
+ * holds partial counters).  The caller's CSR is not validated on the device;
+ * ids out of range are undefined behaviour. */
 sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_col, const int32_t *d_vlabel,
                              const int32_t *d_elabel, int32_t k, int64_t m, const int32_t *src, const int32_t *dst,
                              const int32_t *vlabel, const int32_t *elabel, void *cuda_stream, int64_t time_limit_ms,

@@ -25,8 +25,7 @@
  * paper defines no hash; this one is order-free so that any schedule gives
  * the same value.
  *
- * Readings where the paper is silent or garbled (each also listed in the
- * design notes):
+ * Readings where the paper is silent or garbled:
  *  - w_m is |N(v) intersect mu| (the printed union contradicts the prose).
  *  - The first vertex is the one of highest degree; ties go to the smaller
  *    domain (SI variants only), then to the lower id.  The greedy key is

@@ -2020,9 +2020,21 @@ sge_status sge_enumerate(sge_ctx *ctx, int32_t target_id, int32_t pattern_id, co
     return SGE_OK;
 }
 
-// No device allocation: see include/sge.h.  All host-side work uses fixed
-// arrays on the stack; all device-side data lives in the library's fixed
-// scratch array (sge_noalloc.cu).
+// No device allocation: see include/sge.h.  The pattern's host-side tables
+// (about 200 KB at 128 vertices) live in one host heap block freed on return,
+// so the call needs little stack; all device-side data lives in the library's
+// fixed scratch array (sge_noalloc.cu).
+namespace {
+struct NoallocHost {
+    int amat[KMAX * KMAX];
+    uint64_t nbits[2 * KMAX];
+    int32_t lab[KMAX], odeg[KMAX];
+    int mu[KMAX], par[KMAX];
+    PosInfo pos[KMAX];
+    BackEdge back[KMAX * (KMAX - 1) / 2 + 1];
+};
+}  // namespace
+
 sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_col, const int32_t *d_vlabel,
                              const int32_t *d_elabel, int32_t k, int64_t m, const int32_t *src, const int32_t *dst,
                              const int32_t *vlabel, const int32_t *elabel, void *cuda_stream, int64_t time_limit_ms,
@@ -2034,10 +2046,12 @@ sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
     if (m > 0 && (!src || !dst)) return SGE_ERR_ARG;
     if (k > 0 && !vlabel) return SGE_ERR_ARG;
     if (k == 0 || k > n) return SGE_OK;                  // no match and no search
-    // the pattern, validated into fixed arrays
-    int amat[KMAX * KMAX];
-    uint64_t nbits[2 * KMAX];
-    int32_t lab[KMAX], odeg[KMAX];
+    // the pattern, validated into fixed-size host tables
+    std::unique_ptr<NoallocHost> hbuf(new (std::nothrow) NoallocHost);
+    if (!hbuf) return SGE_ERR_OOM;
+    int *amat = hbuf->amat;
+    uint64_t *nbits = hbuf->nbits;
+    int32_t *lab = hbuf->lab, *odeg = hbuf->odeg;
     bool any_elab = d_elabel != nullptr;
     for (int i = 0; i < k * k; ++i) amat[i] = NO_ARC;
     for (int i = 0; i < 2 * k; ++i) nbits[i] = 0;
@@ -2055,20 +2069,25 @@ sge_status sge_count_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
         odeg[v] = __builtin_popcountll(nbits[2 * v]) + __builtin_popcountll(nbits[2 * v + 1]);
     }
     const PatView P{k, false, lab, odeg, odeg, amat, nbits};
-    int mu[KMAX], par[KMAX];
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int *mu = hbuf->mu, *par = hbuf->par;
     gcf_order_into(P, SGE_RI, nullptr, mu, par);
-    PosInfo pos[KMAX];
-    BackEdge back[KMAX * (KMAX - 1) / 2 + 1];
+    PosInfo *pos = hbuf->pos;
+    BackEdge *back = hbuf->back;
     const int nb = build_positions_into(P, mu, par, SGE_RI, nullptr, n, pos, back);
 
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     void *base = nullptr;
     size_t cap = 0;
     if (noalloc_scratch(&base, &cap) != cudaSuccess) return SGE_ERR_CUDA;
     int32_t nnz = 0;
     const bool zero_elab = any_elab && d_elabel == nullptr;   // labelled pattern, unlabelled target
-    if (zero_elab && cudaMemcpy(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return SGE_ERR_CUDA;
+    if (zero_elab) {
+        // rowptr[n] read on the caller's stream, after whatever the caller queued there to fill it
+        if (cudaMemcpyAsync(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SGE_ERR_CUDA;
+        if (nnz < 0) return SGE_ERR_ARG;
+    }
     // carve the scratch (256-byte aligned pieces)
     constexpr int POOL = 2048;
     size_t off = 0;

@@ -86,15 +86,20 @@ def test_clock_samples_without_a_window_use_the_whole_run():
     assert s["window"] == "whole run" and s["samples"] == 1 and s["sm_mhz"] == 1800 and s["reasons"] == []
 
 
-def test_issue_roofline_follows_the_capture_record():
+def test_search_roofline_follows_the_capture_record():
+    """The roofline names instruction issue as the bound, with the peak from the
+    device's SM count and the sampled clock; the ncu counts appear only while the
+    sources they were taken on are unchanged."""
     sys.path.insert(0, ROOT)
     import bench
     rec = bench._measured_record()
-    r = bench.issue_roofline(5e-3)
-    if not rec:   # kernel source changed since the last capture: nothing is claimed
-        assert r is None and bench._measured_traffic() is None
+    r = bench.search_roofline(5e-3, 14e9, 17e6, 1800.0, 152)
+    assert r["bound"] == "alu" and r["peak"] == 152 * 4 * 1800e6
+    assert abs(r["alg_bytes_frac_of_hbm"] - 14e9 / 5e-3 / 1e9 / r["hbm_peak_gbs"]) < 1e-12
+    if not rec:   # sources changed since the last capture: nothing measured is claimed
+        assert r["frac"] is None and r["traffic"] is None and r["instructions_per_launch"] is None
         return
-    assert r["bound"] == "issue" and r["peak"] == 152 * 4 * 2070e6
     assert r["instructions_per_launch"] == int(rec["warp_instructions_per_launch"])
     assert abs(r["frac"] - r["instructions_per_launch"] / 5e-3 / r["peak"]) < 1e-12
-    assert bench._measured_traffic() == int(rec["dram_bytes_per_launch"])
+    assert r["traffic"] == int(rec["dram_bytes_per_launch"])
+    assert abs(r["instructions_per_search_node"] - r["instructions_per_launch"] / 17e6) < 1e-9

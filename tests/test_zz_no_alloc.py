@@ -76,3 +76,30 @@ def test_noalloc_rejects_a_target_beyond_its_fixed_scratch():
     vlabel = torch.zeros(n, dtype=torch.int32, device="cuda")
     rc, got = sge.sge_count_noalloc(n, rowptr.data_ptr(), col.data_ptr(), vlabel.data_ptr(), 0, complete(3))
     assert rc == sge.SGE_ERR_ARG and got["matches"] == 0
+
+
+def test_noalloc_reads_the_csr_in_order_on_a_nonblocking_stream():
+    """A caller that fills its CSR on its own non-blocking stream and calls at once:
+    every read the entry point makes of that CSR (including rowptr[n], which a
+    labelled pattern on an unlabelled target needs) must wait for the fill.  The
+    fill is held back behind a short spin kernel on that stream."""
+    import torch
+    import paper_1705_09358_gb300 as sge
+    from gpu_common import engine, counters
+    name, t, p = _cases()[3]          # labelled pattern, unlabelled target
+    E = engine()
+    want = counters(E.count(E.load_target(t), E.load_pattern(p), algo=0))
+    ready = _device_csr(t)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()           # created non-blocking: no implicit order with the legacy stream
+    for call in range(2):
+        with torch.cuda.stream(s):
+            d = {key: torch.full_like(v, -1) for key, v in ready.items()}
+            torch.cuda._sleep(20_000_000)             # about 10 ms of device time before the fill
+            for key in d:
+                d[key].copy_(ready[key])
+        rc, got = sge.sge_count_noalloc(t.n, d["rowptr"].data_ptr(), d["col"].data_ptr(), d["vlabel"].data_ptr(),
+                                        0, p, stream=s)
+        assert rc == sge.SGE_OK, (call, rc)
+        assert counters(got) == want, call
+        s.synchronize()
