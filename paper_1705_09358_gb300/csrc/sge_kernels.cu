@@ -1406,10 +1406,15 @@ __host__ __device__ __forceinline__ int list_cap(int kmax) { return kmax <= 32 ?
 constexpr uint8_t LIST_SPILLED = 0xff;
 
 struct __align__(16) PosB {
-    int16_t pv, par, bb, bc;  // pattern vertex, parent position, back-edge range
+    int16_t pv, par, bb, bc;  // pattern vertex, parent position, back edges [bb, bb + bc) other than
+                              // one to position i - 1 (that one, if any, is stored right after them)
     int32_t ucnt;             // raw candidates of an unparented position
-    int32_t abytes;           // algorithmic bytes of one expansion: rows ANDed x dw x 8
+    int32_t abf;              // algorithmic bytes of one expansion (rows ANDed x dw x 8, low 28 bits),
+                              // flags PREV_ADJ / PREV_PAR above them
 };
+constexpr int32_t PREV_ADJ = 1 << 28;   // mu_{i-1} is adjacent to mu_i (as parent or back edge)
+constexpr int32_t PREV_PAR = 1 << 29;   // ... and is its parent
+constexpr int32_t ABYTES_MASK = (1 << 28) - 1;
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
     return round16((size_t)kmax * sizeof(PosB) +            // position table (16-byte aligned)
@@ -1457,53 +1462,69 @@ __device__ __forceinline__ void used_flip(uint64_t (&used)[NWL], int v) {
     }
 }
 
-// Expand position i: compute S_i, count its survivors (the accepted nodes),
-// and either hash them as matches (leaf) or keep them as pending survivors.
-// `st` and `ab` are 32-bit: one expansion adds at most n_t <= 8192 states and
-// (k_max + 1) x 128 x 8 bytes, and the caller folds them into 64-bit totals
-// every 64 expansions.
-template <int NWL, bool RANGE = false>
-__device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, const BitsWarp &W,
-                                           const uint64_t (&used)[NWL], int i, bool leaf,
-                                           unsigned &st, unsigned long long &hs, unsigned &ab,
-                                           int vlo = 0, int vhi = 0x7fffffff, bool count_len = true) {
+// This lane's words of row x of the adjacency bitset, ANDed into s.
+template <int NWL>
+__device__ __forceinline__ void and_row(const uint64_t *adj, int dw, int x, uint64_t (&s)[NWL]) {
+    const uint64_t *X = adj + (size_t)x * dw;
     const int lane = threadIdx.x & 31;
-    const PosB p = W.tab[i];
+#pragma unroll
+    for (int w = 0; w < NWL; ++w) {
+        const int q = lane + 32 * w;
+        if (q < dw) s[w] &= __ldg(X + q);
+    }
+}
+
+// The part of position i's candidate set that does not depend on M[i-1]:
+//   P_i = D(mu_i) & A[M(P(mu_i))] (unless the parent is position i - 1)
+//         & AND over the other back-neighbours j < i - 1 of A[M_j] & ~used
+// (`used` = images of positions 0..i-2).  With `with_prev` the rows of
+// position i - 1 are ANDed too (then `used` must hold M_{i-1} as well), which
+// gives the whole candidate set S_i.  `len` receives the raw candidate count
+// when it does not depend on M[i-1] (else 0).
+template <int NWL>
+__device__ __forceinline__ void bits_rows(const BitsJob &B, const BitsWarp &W, const PosB &p, int i, bool with_prev,
+                                          const uint64_t (&used)[NWL], uint64_t (&s)[NWL], int &len) {
+    const int lane = threadIdx.x & 31;
     const int dw = B.dw;
     const uint64_t *F = B.filt + (size_t)p.pv * dw;
     const int *M = W.M;
-    uint64_t s[NWL];
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
         const int q = lane + 32 * w;
         s[w] = q < dw ? F[q] : 0ull;
     }
-    int len = p.ucnt;
+    len = p.ucnt;
     if (p.par >= 0) {
-        const int a = M[p.par];
-        const uint64_t *A = B.adj + (size_t)a * dw;
-#pragma unroll
-        for (int w = 0; w < NWL; ++w) {
-            const int q = lane + 32 * w;
-            if (q < dw) s[w] &= __ldg(A + q);
+        if (with_prev || !(p.abf & PREV_PAR)) {
+            const int a = M[p.par];
+            and_row<NWL>(B.adj, dw, a, s);
+            len = __ldg(B.vld + a).y;
+        } else {
+            len = 0;
         }
-        len = __ldg(B.vld + a).y;
     }
 #pragma unroll 2
-    for (int b = 0; b < p.bc; ++b) {
-        const uint64_t *X = B.adj + (size_t)M[W.tback[p.bb + b]] * dw;
+    for (int b = 0; b < p.bc; ++b) and_row<NWL>(B.adj, dw, M[W.tback[p.bb + b]], s);
+    if (with_prev && (p.abf & PREV_ADJ) && !(p.abf & PREV_PAR)) and_row<NWL>(B.adj, dw, M[i - 1], s);
 #pragma unroll
-        for (int w = 0; w < NWL; ++w) {
-            const int q = lane + 32 * w;
-            if (q < dw) s[w] &= __ldg(X + q);
-        }
-    }
-    if (count_len) st += (unsigned)len;
-    ab += (unsigned)p.abytes;
+    for (int w = 0; w < NWL; ++w) s[w] &= ~used[w];
+}
+
+// Count the survivors of position i's candidate set s (the accepted nodes) and
+// either hash them as matches (leaf) or keep them as level i's pending
+// survivors: a short list in shared memory, else the bitset in the slab.
+// With none, level i's list is left as it was: the caller does not descend.
+// `st` and `ab` are 32-bit: one expansion adds at most n_t <= 8192 states and
+// (k_max + 1) x 128 x 8 bytes, and the caller folds them into 64-bit totals
+// every 64 expansions.  M[0..i-1] must be in shared memory when the set has
+// matches (the hash and the match rows read them).
+template <int NWL, bool RANGE = false>
+__device__ __forceinline__ int bits_finish(const JobDesc &J, const BitsWarp &W, uint64_t (&s)[NWL], int i, int pv,
+                                           bool leaf, unsigned long long &hs, int vlo = 0, int vhi = 0x7fffffff) {
+    const int lane = threadIdx.x & 31;
     int cnt = 0;
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
-        s[w] &= ~used[w];
         if (RANGE) {
             // a range frame: keep the candidates with vertex ids in [vlo, vhi]
             const int b0 = (lane + 32 * w) * 64;
@@ -1517,9 +1538,10 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
         cnt += __popcll(s[w]);
     }
     const int total = __reduce_add_sync(FULL, (unsigned)cnt);
+    if (total == 0) return 0;
     if (leaf) {
-        if (total == 0) return 0;
         // hash prefix sum_{t < i} g(mu_t, M_t), computed only when matches exist
+        const int *M = W.M;
         unsigned long long ps = 0;
         for (int t = lane; t < i; t += 32) ps += gterm(W.tab[t].pv, M[t]);
         ps = warp_sum(ps);
@@ -1530,16 +1552,13 @@ __device__ __forceinline__ int bits_expand(const BitsJob &B, const JobDesc &J, c
             while (y) {
                 const int bit = __ffsll((long long)y) - 1;
                 const int vtx = q * 64 + bit;
-                hs += fmix64(ps + gterm(p.pv, vtx));
+                hs += fmix64(ps + gterm(pv, vtx));
                 if (J.mbuf) emit_match(J, M, i, vtx);
                 y &= y - 1;
             }
         }
         return total;
     }
-    // pending survivors: a short list in shared memory, else the bitset in the slab.
-    // With none, level i's list is left as it was: the caller does not descend to it.
-    if (total == 0) return 0;
     if (total <= W.lcap) {
         int incl = cnt;
 #pragma unroll
@@ -1651,13 +1670,18 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             for (int t = lane; t < B.k; t += 32) {
                 const PosInfo P = J.pos[t];
                 PosB q;
-                q.pv = (int16_t)P.pv; q.par = (int16_t)P.par; q.bb = (int16_t)P.bbeg; q.bc = (int16_t)P.bcnt;
+                // back edges come in ascending position order, so one to position t - 1 is the last
+                const bool prev_back = P.bcnt > 0 && J.back[P.bbeg + P.bcnt - 1].pos == t - 1;
+                const bool prev_par = t > 0 && P.par == t - 1;
+                q.pv = (int16_t)P.pv; q.par = (int16_t)P.par; q.bb = (int16_t)P.bbeg;
+                q.bc = (int16_t)(P.bcnt - (prev_back ? 1 : 0));
                 q.ucnt = (J.flags & JOB_RIDS) ? P.ucnt : J.t.n;   // RI: all of V_t
-                q.abytes = ((P.par >= 0 ? 2 : 1) + P.bcnt) * J.t.dw * 8;
+                q.abf = ((P.par >= 0 ? 2 : 1) + P.bcnt) * J.t.dw * 8 | (prev_back || prev_par ? PREV_ADJ : 0) |
+                        (prev_par ? PREV_PAR : 0);
                 W.tab[t] = q;
             }
             __syncwarp();
-            const int nb = W.tab[B.k - 1].bb + W.tab[B.k - 1].bc;
+            const int nb = J.pos[B.k - 1].bbeg + J.pos[B.k - 1].bcnt;
             for (int b = lane; b < nb; b += 32) W.tback[b] = (uint8_t)J.back[b].pos;
             __syncwarp();
         }
@@ -1700,16 +1724,34 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         if (lane == 0) { W.frange[0] = fr.beg; W.frange[1] = fr.end; }   // read back only by a checkpoint
         const bool count_len = fr.beg <= 0 && !fr.counted;
         const bool leaf0 = d0 == k - 1;
-        const int c0 = fr.beg >= 0 ? bits_expand<NWL, true>(B, J, W, used, d0, leaf0, st32, hs, ab32, vlo, vhi, count_len)
-                                   : bits_expand<NWL>(B, J, W, used, d0, leaf0, st32, hs, ab32);
+        int c0;
+        {
+            // the frame's first expansion: position d0 with M[0..d0-1] given and all in `used`
+            const PosB p = W.tab[d0];
+            uint64_t s[NWL];
+            int len;
+            bits_rows<NWL>(B, W, p, d0, true, used, s, len);
+            if (count_len) st32 += (unsigned)len;
+            ab32 += (unsigned)(p.abf & ABYTES_MASK);
+            c0 = fr.beg >= 0 ? bits_finish<NWL, true>(J, W, s, d0, p.pv, leaf0, hs, vlo, vhi)
+                             : bits_finish<NWL>(J, W, s, d0, p.pv, leaf0, hs);
+        }
         if (!fr.counted) nd += c0;
         if (leaf0) {
             mt += c0;
         } else if (c0 > 0) {
-            // Levels d0..lvl hold pending survivors; `cur` is M[lvl] (-1 before the
-            // level's first choice).  An expansion that finds no survivors does not
-            // descend, so a level's list is read only after an expansion filled it.
-            int lvl = d0, cur = -1;
+            // Levels d0..lvl hold pending survivors; `used` holds M_0..M_{lvl-1} (not the
+            // choice at lvl).  Pv is the part of position lvl + 1's candidate set that does
+            // not depend on M[lvl] (see bits_rows), valid while `pok`: consecutive siblings
+            // at one level share it, and a descent or ascent invalidates it.  An expansion
+            // that finds no survivors does not descend, so a level's list is read only
+            // after an expansion filled it.
+            int lvl = d0;
+            bool pok = false;
+            uint64_t Pv[NWL];
+            int plen = 0;
+#pragma unroll
+            for (int w = 0; w < NWL; ++w) Pv[w] = 0ull;
             for (;;) {
                 if (((++iter) & 63) == 0) {
                     st += st32; nd += nd32; mt += mt32; ab += ab32;
@@ -1746,28 +1788,61 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         donation_done(C);
                     }
                 }
-                if (cur >= 0) used_flip<NWL>(used, cur);        // leave the previous choice at this level
                 const int v = bits_next<NWL>(W, lvl);
                 if (v < 0) {
                     if (lvl == d0) break;
                     --lvl;
-                    cur = M[lvl];
+                    used_flip<NWL>(used, M[lvl]);   // the choice at the new current level leaves `used`
+                    pok = false;
                     continue;
                 }
-                used_flip<NWL>(used, v);
-                if (lane == 0) M[lvl] = v;
-                __syncwarp();
-                const bool leaf = lvl + 1 == k - 1;
-                const int c = bits_expand<NWL>(B, J, W, used, lvl + 1, leaf, st32, hs, ab32);
-                nd32 += c;
-                if (leaf) {
-                    mt32 += c;
-                    cur = v;
-                } else if (c > 0) {
-                    ++lvl;
-                    cur = -1;
+                const int i = lvl + 1;
+                const PosB p = W.tab[i];
+                if (!pok) {
+                    bits_rows<NWL>(B, W, p, i, false, used, Pv, plen);
+                    pok = true;
+                }
+                uint64_t s[NWL];
+#pragma unroll
+                for (int w = 0; w < NWL; ++w) s[w] = Pv[w];
+                int len = plen;
+                if (p.abf & PREV_ADJ) {
+                    and_row<NWL>(B.adj, B.dw, v, s);   // A[v] never holds v itself
+                    if (p.abf & PREV_PAR) len = __ldg(B.vld + v).y;
                 } else {
-                    cur = v;
+                    uint64_t nv[NWL];
+#pragma unroll
+                    for (int w = 0; w < NWL; ++w) nv[w] = ~0ull;
+                    used_flip<NWL>(nv, v);
+#pragma unroll
+                    for (int w = 0; w < NWL; ++w) s[w] &= nv[w];
+                }
+                st32 += (unsigned)len;
+                ab32 += (unsigned)(p.abf & ABYTES_MASK);
+                const bool leaf = i == k - 1;
+                if (leaf) {
+                    // the match rows and the hash read M[0..i-1]: store the choice first when
+                    // the set is not empty
+                    int any = 0;
+#pragma unroll
+                    for (int w = 0; w < NWL; ++w) any |= s[w] != 0ull;
+                    if (__any_sync(FULL, any)) {
+                        if (lane == 0) M[lvl] = v;
+                        __syncwarp();
+                    }
+                    const int c = bits_finish<NWL>(J, W, s, i, p.pv, true, hs);
+                    nd32 += c;
+                    mt32 += c;
+                } else {
+                    const int c = bits_finish<NWL>(J, W, s, i, p.pv, false, hs);
+                    nd32 += c;
+                    if (c > 0) {
+                        if (lane == 0) M[lvl] = v;
+                        __syncwarp();
+                        used_flip<NWL>(used, v);
+                        lvl = i;
+                        pok = false;
+                    }
                 }
             }
             if (stopped && C.ckpt != nullptr) {
