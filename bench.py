@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Throughput benchmark: search states/sec (and matches/sec) on one GB300.
 
-Default workload (the dense RI-DS configuration): target G(2000, 0.05) with
+Headline workload (the dense RI-DS configuration): target G(2000, 0.05) with
 4 uniform vertex labels, five dense-walk patterns of 16, 18, 20, 22 and 24
 vertices, RI-DS-SI-FC.  One step = one batched launch sequence over the five
 (target, pattern) pairs through the C ABI: domains (init, arc consistency,
@@ -9,13 +9,21 @@ forward checking), ordering, breadth-first split and the persistent search.
 Inputs are resident in device memory before timing; L2 is flushed (256 MB
 write) between timed steps.  The line also carries the end-to-end number
 (host buffers in, results out, through the public API), the roofline of the
-persistent search kernel, the CPU oracle on a bounded sample, and the
-batched-vs-per-query speedup on a sample of the molecule workload.
+persistent search kernel, and (N = 1) the other workloads -- the single
+plain-RI query, the 10k-vertex power-law target with RI and RI-DS-SI-FC, all
+200,000 molecule pairs (autotuned batched call, library defaults, one call
+per pair) and the 5000-query serving stream -- with the CPU oracle as
+baseline: one thread on a bounded sample of the headline workload, and one
+instance per thread over all host cores for the batched and served ones.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --tune er2000,cl10k,cl10k-ri,mol200,cl100k [--tune-out PATH]
+    python bench.py --ablation
 
-With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of
-the workload (weak scaling); ranks exchange only the timing maximum.
+With N > 1 (torchrun, one rank per GPU) the split frontier is sharded over
+the ranks (frame i to rank i mod N, the paper's subtrees being independent)
+and the four counters are summed once per step (strong scaling);
+``--replicas`` runs the whole workload on every rank instead (weak scaling).
 """
 from __future__ import annotations
 
@@ -269,10 +277,129 @@ def search_roofline(kernel_s: float, alg_bytes: float, nodes: float, sm_mhz, sms
     return out
 
 
+def host_cpu() -> dict:
+    """Host cores this process may use and the CPU model (lscpu, else /proc/cpuinfo)."""
+    import platform
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": usable, "cpu_count": os.cpu_count(), "model": model or platform.processor() or "unknown",
+            "machine": platform.machine()}
+
+
+# ------------------------------------------------- process-pool workers (spawned)
+_W = {}
+
+
+def _gen_cl100k_chunk(lo: int, hi: int) -> list:
+    """Queries lo..hi-1 of the 100k-vertex serving stream (generated in a worker)."""
+    from gen import configs
+    from gen.patterns import _Adj
+    if "cl100k" not in _W:
+        t = configs.cl100k_target()
+        _W["cl100k"] = (t, _Adj(t), configs.cl100k_sizes(5000), configs.load_admitted().get("cl100k", {}))
+    t, adj, ks, adm = _W["cl100k"]
+    return [configs.cl100k_candidate(t, i, int(ks[i]), int(adm.get(str(i), 0)), adj) for i in range(lo, hi)]
+
+
+def _oracle_mol_chunk(idx: list) -> tuple:
+    """The oracle (one thread) on the listed mol200 pairs (target index, pattern index)."""
+    import oracle
+    from gen import configs
+    if "mol" not in _W:
+        ts = configs.mol_targets(200)
+        _W["mol"] = ([oracle.Target(t) for t in ts], configs.mol_patterns(ts, 1000))
+    ots, ps = _W["mol"]
+    s = m = 0
+    t0 = time.perf_counter()
+    for ti, pi in idx:
+        r = oracle.run(ots[ti], ps[pi], 0)
+        s += r["states"]
+        m += r["matches"]
+    return s, m, time.perf_counter() - t0
+
+
+def _oracle_cl100k_chunk(patterns: list) -> tuple:
+    import oracle
+    from gen import configs
+    if "cl100k_oracle" not in _W:
+        _W["cl100k_oracle"] = oracle.Target(configs.cl100k_target())
+    ot = _W["cl100k_oracle"]
+    s = m = 0
+    t0 = time.perf_counter()
+    for p in patterns:
+        r = oracle.run(ot, p, 0)
+        s += r["states"]
+        m += r["matches"]
+    return s, m, time.perf_counter() - t0
+
+
+def spawn_pool():
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(max(1, host_cpu()["nproc"]))
+
+
+def cl100k_queries(pool, count: int) -> list:
+    chunks = [(lo, min(count, lo + 50)) for lo in range(0, count, 50)]
+    out = []
+    for part in pool.starmap(_gen_cl100k_chunk, chunks):
+        out.extend(part)
+    return out
+
+
+def oracle_throughput(pool, cl100k_patterns) -> dict:
+    """The benchmark's throughput plan for the batched and served workloads: the oracle as it
+    stands, one instance per thread, spread over every host core of the GPU machine."""
+    cores = host_cpu()["nproc"]
+    out = {}
+    pairs = [(ti, pi) for ti in range(200) for pi in range(1000)]
+    chunks = [pairs[i::cores * 8] for i in range(cores * 8)]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_mol_chunk, chunks)
+    wall = time.perf_counter() - t0
+    s = sum(r[0] for r in res)
+    out["mol200"] = {"value": s / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                     "matches_per_sec": sum(r[1] for r in res) / wall, "states": s, "seconds": wall,
+                     "sample": "all 200,000 (target, pattern) pairs, RI, one pair per oracle call, "
+                               f"spread over {cores} worker processes (includes each worker's setup)"}
+    sample = cl100k_patterns[:1000]
+    chunks = [sample[i::cores * 4] for i in range(cores * 4)]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_cl100k_chunk, chunks)
+    wall = time.perf_counter() - t0
+    s = sum(r[0] for r in res)
+    out["cl100k"] = {"value": s / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                     "matches_per_sec": sum(r[1] for r in res) / wall, "states": s, "seconds": wall,
+                     "sample": f"the first 1000 of the 5000 queries, RI, spread over {cores} worker processes"}
+    return out
+
+
+# ---------------------------------------------------------------- our arm
 def run_ours(args, world, rank, local):
     import torch
     import paper_1705_09358_gb300 as sge
+    from paper_1705_09358_gb300 import shard
     from gen import configs
+    extras = rank == 0 and world == 1 and not args.no_extras
+    pool = spawn_pool() if extras else None        # started before the first GPU call
     sge.build.build()
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
@@ -283,10 +410,16 @@ def run_ours(args, world, rank, local):
     pids = [E.load_pattern(p) for p in w.patterns]
     tids = [tid] * len(pids)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    sharded = world > 1 and not args.replicas
+    sh = {"shard_index": rank, "shard_count": world} if sharded else {}
 
-    def step():
-        rc, rows = E.count_batch(tids, pids, algo=ALGO)
-        return rows
+    def step(ti=tids, pi=pids):
+        rc, rows = E.count_batch(ti, pi, algo=ALGO, **sh)
+        if sharded:
+            # the one exchange step of the sharded search: a wrapping sum of the four counters
+            tot = shard.reduce_counters({k: int(rows[k].sum()) % (1 << 64) for k in shard.KEYS})
+            return rows, tot
+        return rows, {k: int(rows[k].sum()) % (1 << 64) for k in shard.KEYS}
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -296,31 +429,36 @@ def run_ours(args, world, rank, local):
     states = matches = alg_bytes = launches = nodes = 0
     kernel_ms = 0.0
     kernel_launches = 0
+    last = None
     with Clocks(local) as clk:
         clk.start()
         with torch.cuda.stream(stream):
             for i in range(args.steps):
                 flush.zero_()                       # evict L2 between timed steps
                 ev[i][0].record(stream)
-                rows = step()
+                rows, tot = step()
                 ev[i][1].record(stream)
-                states += int(rows["states"].sum())
-                matches += int(rows["matches"].sum())
+                states += tot["states"]
+                matches += tot["matches"]
                 alg_bytes += int(rows["alg_bytes"].sum())
                 nodes += int(rows["nodes"].sum())
                 launches += int(rows["launches"][0])
                 kernel_ms += float(rows["search_kernel_ms"][0])
                 kernel_launches += 1
+                last = tot
         barrier(world)
         clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1000.0
     total_s = max_over_ranks(total_s, world)
-    value = world * states / total_s
+    job_states = states if sharded else world * states     # replicas each do the whole job
+    value = job_states / total_s
     clocks = clk.summary()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roofline = search_roofline(kernel_ms / kernel_launches / 1000.0, alg_bytes / kernel_launches,
                                nodes / kernel_launches, clocks.get("sm_mhz"), sms)
+    golden = _golden_totals("er2000", ALGO)
+    agrees = golden is None or tuple(last[k] for k in shard.KEYS) == golden
 
     # ------------------------------------------------------ end to end
     def pinned(a):
@@ -344,42 +482,148 @@ def run_ours(args, world, rank, local):
             flush.zero_()
             tt = sge.sge_load_target(E.h, t.n, tp[0], tp[1], tp[2], tp[3], False)
             pp = [sge.sge_load_pattern(E.h, n, s, d, v, e, False) for n, s, d, v, e in srcs]
-            rc, rows = E.count_batch([tt] * len(pp), pp, algo=ALGO)
-            e2e_states += int(rows["states"].sum())
+            rows, tot = step([tt] * len(pp), pp)
+            e2e_states += tot["states"]
             for x in pp:
                 sge.sge_unload_pattern(E.h, x)
             sge.sge_unload_target(E.h, tt)
     barrier(world)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": world * e2e_states / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h),
+    e2e = {"value": (e2e_states if sharded else world * e2e_states) / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "note": "sge_load_target (device ingest) + 5 x sge_load_pattern from pinned host arrays, "
                    "sge_count_batch, results to host, unload"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"replicas x{world}"},
-            "matches_per_sec": world * matches / total_s,
-            "states_per_step": states // args.steps, "matches_per_step": matches // args.steps,
+                       "parallelism": (f"split frontier sharded over {world} GPUs (frame i -> rank i mod {world}), "
+                                       "one 4-counter sum per step") if sharded else f"replicas x{world}"},
+            "matches_per_sec": (matches if sharded else world * matches) / total_s,
+            "states_per_step": job_states // args.steps // (1 if sharded else world),
+            "matches_per_step": (matches if sharded else world * matches) // args.steps // (1 if sharded else world),
+            "counters_equal_oracle_golden": agrees,
             "gpu_launches": launches, "roofline": roofline, "e2e": e2e}
-    if rank == 0 and world == 1 and not args.no_extras:
-        line["batched_vs_per_query"] = batched_vs_per_query(E, args)
-        line["serving"] = serving_latency(E)
+    if extras:
+        queries = cl100k_queries(pool, args.cl100k_queries)
+        line["workloads"] = {"er1000": measure_er1000(E), "cl10k": measure_cl10k(E), "mol200": measure_mol200(E),
+                             "cl100k": measure_cl100k(E, queries)}
+        line["batched_vs_per_query"] = line["workloads"]["mol200"]["speedup_vs_per_query"]
+        line["serving"] = line["workloads"]["cl100k"]["serving"]
         smp = oracle_sample(w, 200_000_000)
+        cpu = host_cpu()
         line["cpu_baseline"] = {"value": smp["states"] / smp["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "host": cpu,
                                 "sample": "the oracle (one thread) on all 5 patterns, each stopped after 2e8 states; "
                                           f"{smp['states']} states in {smp['seconds']:.1f} s"}
+        line["cpu_baseline_throughput"] = oracle_throughput(pool, queries)
+        pool.close()
     line["clocks"] = clocks
     E.close()
+    if not agrees:
+        print(json.dumps({"error": "counters differ from the oracle's stored values", "got": last}), file=sys.stderr)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def batched_vs_per_query(E, args) -> dict:
-    """Molecule workload: all 200,000 (target, pattern) pairs in one batched
-    call vs one call per pair (per-pair rate from an evenly spaced sample)."""
+def _golden_totals(name: str, algo: int):
+    """Summed (matches, states, nodes, hash mod 2^64) of a workload from the stored oracle results."""
+    path = os.path.join(ROOT, "tests", "golden", f"expected_{name}.json")
+    try:
+        g = json.load(open(path))
+    except OSError:
+        return None
+    ents = g["patterns"] if "patterns" in g else [g]
+    tot = [0, 0, 0, 0]
+    for e in ents:
+        a = e["algos"][str(algo)]
+        for i, k in enumerate(("matches", "states", "nodes", "hash")):
+            tot[i] = (tot[i] + int(a[k])) % (1 << 64)
+    return tuple(tot)
+
+
+def _timed_batch(E, tids, pids, reps: int = 5, **opts):
+    """Median wall time of a batched call (the call returns with its device work done)."""
+    import torch
+    E.count_batch(tids, pids, **opts)
+    best = []
+    rows = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, rows = E.count_batch(tids, pids, **opts)
+        torch.cuda.synchronize()
+        best.append(time.perf_counter() - t0)
+    return statistics.median(best), rows
+
+
+def _batch_line(dt, rows, **extra) -> dict:
+    states = int(rows["states"].sum())
+    d = {"seconds": dt, "states_per_s": states / dt, "matches_per_s": int(rows["matches"].sum()) / dt,
+         "states": states, "matches": int(rows["matches"].sum()),
+         "split_kernel_ms": float(rows["split_kernel_ms"][0]), "search_kernel_ms": float(rows["search_kernel_ms"][0]),
+         "preprocess_ms": float(rows["preprocess_ms"][0]), "split_depth": int(rows["split_depth"][0]),
+         "kernel": "bitset" if int(rows["kernel"][0]) == 2 else "csr", "launches": int(rows["launches"][0])}
+    # the path's device kernels (split + search): algorithmic bytes per state of the CSR path
+    # (4-byte candidate id + 8-byte {label, degree} record) over their device time
+    dev_s = (d["split_kernel_ms"] + d["search_kernel_ms"]) / 1000.0
+    if d["kernel"] == "csr" and dev_s > 0:
+        hbm, kind = _peaks()
+        gbs = 12.0 * states / dev_s / 1e9
+        d["roofline"] = {"bound": "latency (frontier levels and grid barriers; data L2-resident)",
+                         "alg_bytes_gbs": gbs, "alg_bytes_frac_of_hbm": gbs / hbm,
+                         "bytes_per_state": 12, "device_ms": dev_s * 1000.0,
+                         "hbm_peak_gbs": hbm, "hbm_peak_kind": f"of {kind} HBM copy"}
+    d.update(extra)
+    return d
+
+
+def measure_er1000(E) -> dict:
+    """Config 1: plain RI, one query, full sorted match list, one call per query."""
+    import torch
+    from gen import configs
+    w = configs.er1000()
+    tid, pid = E.load_target(w.targets[0]), E.load_pattern(w.patterns[0])
+    E.enumerate(tid, pid, algo=0)
+    lat = []
+    for _ in range(20):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = E.enumerate(tid, pid, algo=0)
+        lat.append(time.perf_counter() - t0)
+    dt = statistics.median(lat)
+    want = _golden_totals("er1000", 0)
+    return {"workload": "er1000: G(1000, 8/999), 8 labels, one 8-vertex random-walk pattern, RI, full sorted match list",
+            "latency_ms": dt * 1000.0, "states_per_s": r["states"] / dt, "matches_per_s": r["matches"] / dt,
+            "matches": r["matches"], "states": r["states"], "rows": int(r["match_list"].shape[0]),
+            "counters_equal_oracle_golden": want is None or
+            (r["matches"], r["states"], r["nodes"], r["hash"]) == want}
+
+
+def measure_cl10k(E) -> dict:
+    """Config 3: RI and RI-DS-SI-FC on the 10k-vertex power-law target, 10 patterns per batch."""
+    from gen import configs
+    w = configs.cl10k()
+    tid = E.load_target(w.targets[0])
+    pids = [E.load_pattern(p) for p in w.patterns]
+    out = {"workload": "cl10k: Chung-Lu n=10,000, gamma 2.3, mean degree 20, 32 Zipf labels; 10 dense-walk "
+                       "patterns of 32/48/64 vertices, all 10 in one batched call"}
+    sums = {}
+    for algo, name in ((0, "RI"), (3, "RI-DS-SI-FC")):
+        dt, rows = _timed_batch(E, [tid] * len(pids), pids, algo=algo)
+        out[name] = _batch_line(dt, rows)
+        sums[algo] = (int(rows["matches"].sum()), int(rows["hash"].sum()) % (1 << 64))
+        want = _golden_totals("cl10k", algo)
+        got = tuple(int(rows[k].sum()) % (1 << 64) for k in ("matches", "states", "nodes", "hash"))
+        out[name]["counters_equal_oracle_golden"] = want is None or got == want
+    out["ri_and_rids_agree"] = sums[0] == sums[3]
+    return out
+
+
+def measure_mol200(E) -> dict:
+    """Config 4: all 200,000 (target, pattern) pairs: autotuned batched call, the library
+    defaults, and one call per pair (per-pair rate from an evenly spaced sample)."""
     import torch
     from gen import configs
     ts = configs.mol_targets(200)
@@ -388,64 +632,44 @@ def batched_vs_per_query(E, args) -> dict:
     pids = [E.load_pattern(p) for p in ps]
     T = np.repeat(np.array(tids, np.int32), len(pids))
     P = np.tile(np.array(pids, np.int32), len(tids))
-    E.count_batch(T[:4096], P[:4096])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rc, rows = E.count_batch(T, P)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    sb = int(rows["states"].sum())
+    tuned_opts = E.tuned_schedule(T, P, 0)
+    dt_t, rows_t = _timed_batch(E, T, P, reps=3, algo=0)
+    dt_d, rows_d = _timed_batch(E, T, P, reps=3, algo=0, tuned=False)
+    same = all(np.array_equal(rows_t[k], rows_d[k]) for k in ("matches", "states", "nodes", "hash"))
     idx = np.arange(0, len(T), 100)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     s1 = 0
     for i in idx:
         s1 += E.count(int(T[i]), int(P[i]))["states"]
     torch.cuda.synchronize()
     t1 = time.perf_counter() - t0
-    b_rate, q_rate = sb / tb, s1 / t1
-    return {"workload": "mol200: 200 molecule-shaped targets x 1000 patterns, RI, all 200,000 pairs",
-            "pairs_batched": int(len(T)), "batched_seconds": tb, "batched_states_per_s": b_rate,
-            "pairs_per_query_sample": int(len(idx)), "per_query_ms_per_pair": 1000.0 * t1 / len(idx),
-            "per_query_states_per_s": q_rate, "speedup": b_rate / q_rate}
+    q_rate = s1 / t1
+    tuned = _batch_line(dt_t, rows_t, schedule=tuned_opts or "library defaults (no tuned point for this class)")
+    dflt = _batch_line(dt_d, rows_d, schedule="library defaults")
+    dt_r, rows_r = _timed_batch(E, T, P, reps=1, algo=3)
+    speed = {"workload": "mol200: 200 molecule-shaped targets x 1000 patterns, RI, all 200,000 pairs",
+             "pairs_batched": int(len(T)), "batched_seconds": dt_t, "batched_states_per_s": tuned["states_per_s"],
+             "pairs_per_query_sample": int(len(idx)), "per_query_ms_per_pair": 1000.0 * t1 / len(idx),
+             "per_query_states_per_s": q_rate, "speedup": tuned["states_per_s"] / q_rate}
+    return {"workload": "mol200: 200 near-tree targets (20-500 vertices) x 1000 random-walk patterns (4-64 "
+                        "vertices), edge labels, all 200,000 pairs",
+            "autotuned_batched": tuned, "default_batched": dflt,
+            "per_query": {"states_per_s": q_rate, "ms_per_pair": 1000.0 * t1 / len(idx), "pairs_sampled": int(len(idx))},
+            "tuned_vs_default": dflt["seconds"] / dt_t, "tuned_vs_per_query": tuned["states_per_s"] / q_rate,
+            "tuned_and_default_counters_equal": same,
+            "RI-DS-SI-FC_batched": _batch_line(dt_r, rows_r),
+            "speedup_vs_per_query": speed}
 
 
-def serving_latency(E, n_queries: int = 1000) -> dict:
-    """Serving on the 100k-vertex power-law target: queries arrive as a
-    Poisson stream and are admitted by the engine's continuous-batching
-    scheduler; latency is submit-to-completion.  The offered load is 0.8 x
-    the serving path's own saturation throughput (every query submitted at
-    once); the batched and one-query-per-call rates are reported beside it."""
-    from gen import configs
-    t = configs.cl100k_target()
-    w = configs.cl100k(count=n_queries, target=t)
-    tid = E.load_target(t)
-    pids = [E.load_pattern(p) for p in w.patterns]
-    n = len(pids)
-    E.count_batch([tid] * 64, pids[:64])
-    t0 = time.perf_counter()
-    rc, rows = E.count_batch([tid] * n, pids)
-    tb = time.perf_counter() - t0
-    total_states = int(rows["states"].sum())
-    # one query per call, back to back, on an evenly spaced sample
-    sample = list(range(0, n, 5))
-    t0 = time.perf_counter()
-    s_seq = sum(E.count(tid, pids[i])["states"] for i in sample)
-    t_seq = time.perf_counter() - t0
-    # warm the scheduler threads, then measure saturation
-    for tk in [E.serve_submit(tid, pids[i]) for i in range(8)]:
-        pass
-    E.serve_drain()
-    t0 = time.perf_counter()
-    sat = [E.serve_submit(tid, pid) for pid in pids]
-    E.serve_drain()
-    t_sat = time.perf_counter() - t0
-    for tk in sat:
-        E.serve_poll(tk)
-    lam = 0.8 * n / t_sat
-    arrivals = configs.cl100k_arrivals(n, lam)
+def serve_stream(E, tid, pids, rate: float, arrivals) -> dict:
+    """Submit queries at the given Poisson arrival times.  Per query: latency (submit to done)
+    and its parts -- queue (submit to admission into a launch group), the group's host work,
+    its kernels' own execution (device clock spans) and the time those kernels waited for SMs
+    held by other groups (event time minus span)."""
     tickets = []
     start = time.perf_counter()
-    for i in range(n):
+    for i in range(len(pids)):
         due = start + float(arrivals[i])
         while True:
             now = time.perf_counter()
@@ -457,19 +681,62 @@ def serving_latency(E, n_queries: int = 1000) -> dict:
     E.serve_drain()
     makespan = time.perf_counter() - start
     res = [E.serve_poll(tk) for tk in tickets]
-    lat = np.array([r["latency_ms"] for r in res])
-    bad = sum(1 for r in res if r["status"] != 0)
-    bad_status = sorted({int(r["status"]) for r in res if r["status"] != 0})
-    served_states = sum(r["states"] for r in res)
-    return {"workload": f"cl100k: Chung-Lu n=100,000 target, first {n} of the 5000 queries (8-128 vertices), RI",
-            "queries": n, "arrival": "Poisson", "offered_qps": lam,
-            "offered_load": "0.8 x serving saturation throughput", "saturation_qps": n / t_sat,
-            "batched_qps": n / tb, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "errors": bad, "error_statuses": bad_status,
-            "served_states_per_s": served_states / makespan,
-            "makespan_s": makespan, "batched_states_per_s": total_states / tb,
-            "sequential_per_query_states_per_s": s_seq / t_seq,
-            "served_vs_sequential": (served_states / makespan) / (s_seq / t_seq)}
+    col = lambda key: np.array([r[key] for r in res], dtype=np.float64)
+    lat, queue = col("latency_ms"), col("queue_ms")
+    service = col("preprocess_ms") + col("match_ms")
+    dev_exec = col("split_exec_ms") + col("search_exec_ms")
+    dev_wait = np.maximum(0.0, col("split_kernel_ms") + col("search_kernel_ms") - dev_exec)
+    host = np.maximum(0.0, service - dev_exec - dev_wait)
+    bad = [int(r["status"]) for r in res if r["status"] != 0]
+    states = sum(r["states"] for r in res)
+    worst = np.argsort(lat)[-max(1, len(lat) // 100):]
+    pct = lambda a, q: float(np.percentile(a, q))
+    parts = {"queue": queue, "host": host, "device_exec": dev_exec, "device_wait": dev_wait}
+    out = {"offered_qps": rate, "queries": len(pids), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+           "mean_ms": float(lat.mean()),
+           "service_p50_ms": pct(service, 50), "service_p99_ms": pct(service, 99),
+           "parts_p50_ms": {k: pct(v, 50) for k, v in parts.items()},
+           "parts_p99_ms": {k: pct(v, 99) for k, v in parts.items()},
+           "slowest_1pct_mean_ms": {"latency": float(lat[worst].mean()),
+                                    **{k: float(v[worst].mean()) for k, v in parts.items()}},
+           "errors": len(bad), "error_statuses": sorted(set(bad)), "makespan_s": makespan,
+           "served_states_per_s": states / makespan, "states": states}
+    return out
+
+
+def measure_cl100k(E, queries) -> dict:
+    """Config 5: the query stream against the device-resident 100k-vertex target: saturation
+    (everything submitted at once), a Poisson stream at 0.8 x saturation, the batched call and
+    one query per call."""
+    from gen import configs
+    t = configs.cl100k_target()
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in queries]
+    n = len(pids)
+    dt_b, rows = _timed_batch(E, [tid] * n, pids, reps=1, algo=0)
+    sample = list(range(0, n, 10))
+    t0 = time.perf_counter()
+    s_seq = sum(E.count(tid, pids[i])["states"] for i in sample)
+    t_seq = time.perf_counter() - t0
+    for _ in range(2):       # warm the scheduler threads and their workspaces
+        E.serve_submit(tid, pids[0])
+        E.serve_drain()
+    t0 = time.perf_counter()
+    sat = [E.serve_submit(tid, pid) for pid in pids]
+    E.serve_drain()
+    t_sat = time.perf_counter() - t0
+    for tk in sat:
+        E.serve_poll(tk)
+    lam = 0.8 * n / t_sat
+    serving = serve_stream(E, tid, pids, lam, configs.cl100k_arrivals(n, lam))
+    serving.update({"workload": f"cl100k: Chung-Lu n=100,000 target, all {n} queries (8-128 vertices), RI",
+                    "arrival": "Poisson", "offered_load": "0.8 x serving saturation throughput",
+                    "saturation_qps": n / t_sat, "batched_qps": n / dt_b,
+                    "sequential_per_query_states_per_s": s_seq / t_seq,
+                    "served_vs_sequential": serving["served_states_per_s"] / (s_seq / t_seq)})
+    return {"workload": f"cl100k: {n} queries against the device-resident 100k-vertex target",
+            "batched": _batch_line(dt_b, rows), "sequential_per_query_states_per_s": s_seq / t_seq,
+            "serving": serving}
 
 
 def run_ablation(args):
@@ -508,6 +775,52 @@ def run_ablation(args):
     E.close()
 
 
+def _workload_pairs(E, name: str, cl100k_queries: int = 5000):
+    """(target ids, pattern ids, variant) of a named workload, loaded into E."""
+    from gen import configs
+    if name == "er2000":
+        w = configs.er2000()
+        tid = E.load_target(w.targets[0])
+        return [tid] * len(w.patterns), [E.load_pattern(p) for p in w.patterns], 3
+    if name in ("cl10k", "cl10k-ri"):
+        w = configs.cl10k()
+        tid = E.load_target(w.targets[0])
+        return [tid] * len(w.patterns), [E.load_pattern(p) for p in w.patterns], 3 if name == "cl10k" else 0
+    if name == "mol200":
+        ts = configs.mol_targets(200)
+        ps = configs.mol_patterns(ts, 1000)
+        tids = [E.load_target(t) for t in ts]
+        pids = [E.load_pattern(p) for p in ps]
+        return np.repeat(np.array(tids, np.int32), len(pids)), np.tile(np.array(pids, np.int32), len(tids)), 0
+    if name == "cl100k":
+        t = configs.cl100k_target()
+        w = configs.cl100k(count=cl100k_queries, target=t)
+        tid = E.load_target(t)
+        return [tid] * len(w.patterns), [E.load_pattern(p) for p in w.patterns], 0
+    raise ValueError(name)
+
+
+def run_tune(args):
+    """Tune the schedule of each named workload (coordinate descent, whole-call time) and
+    write the tuned points, keyed by workload class, to args.tune_out."""
+    import paper_1705_09358_gb300 as sge
+    from paper_1705_09358_gb300 import autotune
+    sge.build.build()
+    E = sge.Context(0)
+    cache = autotune.load(args.tune_out) if os.path.exists(args.tune_out) else {}
+    for name in args.tune.split(","):
+        tids, pids, algo = _workload_pairs(E, name, args.cl100k_queries)
+        out = autotune.tune_batch(E, tids, pids, algo=algo, reps=3, path=None)
+        cache[out["key"]] = {"opts": out["opts"], "seconds": out["seconds"],
+                             "default_seconds": out["default_seconds"], "workload": name}
+        autotune.save(cache, args.tune_out)
+        print(json.dumps({"tune": name, "key": out["key"], "opts": out["opts"], "seconds": out["seconds"],
+                          "default_seconds": out["default_seconds"], "points": len(out["table"]),
+                          "tuning_seconds": out["tuning_seconds"],
+                          "table": sorted(out["table"], key=lambda r: r["seconds"])[:8]}), flush=True)
+    E.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,10 +828,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the CPU baseline and batched comparison")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 GPUs: every rank runs the whole workload (weak scaling) instead of a shard")
     ap.add_argument("--ablation", action="store_true", help="variant comparison instead of the throughput line")
+    ap.add_argument("--tune", default="", help="comma-separated workloads to tune (er2000, cl10k, mol200, cl100k)")
+    ap.add_argument("--tune-out", default=os.path.join(ROOT, "paper_1705_09358_gb300", "autotune_cache.json"))
+    ap.add_argument("--cl100k-queries", type=int, default=5000)
     args = ap.parse_args()
     if args.ablation:
         run_ablation(args)
+        return
+    if args.tune:
+        run_tune(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -85,8 +85,17 @@ typedef struct {
     int32_t donate_every_iters;/* a warp donates at most once per this many search iterations ... */
     int32_t donate_every_us;   /* ... or once per this many microseconds, whichever comes first
                                   (defaults: CSR kernel 1024 / 500, bitset kernel 2^30 / 50) */
-    int32_t reserved[3];
+    int32_t domain_fixpoint;   /* RI-DS domains (arc consistency with forward checking, Section 4):
+                                  0 = auto (SGE_DOMAIN_BLOCKS when the batch holds at least half as
+                                  many RI-DS pairs as the device has SMs and every target has at
+                                  most 16384 vertices, else SGE_DOMAIN_SWEEPS),
+                                  SGE_DOMAIN_SWEEPS = sweeps over the whole device under a host
+                                  loop, SGE_DOMAIN_BLOCKS = each pair's whole fixpoint in one block
+                                  of one launch; both reach the same fixpoint */
+    int32_t reserved[2];
 } sge_opts;
+
+enum { SGE_DOMAIN_AUTO = 0, SGE_DOMAIN_SWEEPS = 1, SGE_DOMAIN_BLOCKS = 2 };
 
 /* Result of one (target, pattern) search.
  *  matches: number of injections found.
@@ -115,7 +124,13 @@ typedef struct {
     int32_t split_depth;     /* depth of that frontier */
     int32_t status;          /* SGE_OK or the error of this pair */
     int32_t kernel;          /* SGE_KERNEL_CSR or SGE_KERNEL_BITSET as used */
-    int32_t reserved[3];
+    float split_kernel_ms;   /* device time of the breadth-first split kernel (CUDA events; 0 if it
+                                did not run as one cooperative launch) */
+    float queue_ms;          /* serving: from sge_serve_submit to admission into a launch group */
+    float split_exec_ms;     /* the split and search kernels' own spans (device clock, first block's */
+    float search_exec_ms;    /* start to last block's end); the event times minus these spans are the
+                                time the kernels waited for SMs held by other work */
+    int32_t reserved[1];
 } sge_result;
 
 /* Match sink: receives `count` matches, each k int32 target ids giving the

@@ -24,6 +24,7 @@ SGE_ERR_ARG, SGE_ERR_OOM, SGE_ERR_CUDA, SGE_ERR_BUDGET = -1, -2, -3, -4
 SGE_ERR_TIMEOUT, SGE_ERR_CANCELLED, SGE_ERR_STOPPED, SGE_ERR_NOT_FOUND = -5, -6, -7, -8
 SGE_RI, SGE_RIDS, SGE_RIDS_SI, SGE_RIDS_SI_FC = 0, 1, 2, 3
 SGE_KERNEL_AUTO, SGE_KERNEL_CSR, SGE_KERNEL_BITSET = 0, 1, 2
+SGE_DOMAIN_AUTO, SGE_DOMAIN_SWEEPS, SGE_DOMAIN_BLOCKS = 0, 1, 2
 
 ERROR_NAMES = {0: "OK", -1: "ARG", -2: "OOM", -3: "CUDA", -4: "BUDGET", -5: "TIMEOUT", -6: "CANCELLED",
                -7: "STOPPED", -8: "NOT_FOUND"}
@@ -40,7 +41,7 @@ class sge_opts(C.Structure):
                 ("steal_granularity", C.c_int32), ("state_budget", C.c_int64), ("time_limit_ms", C.c_int64),
                 ("kernel", C.c_int32), ("blocks_per_sm", C.c_int32), ("shard_index", C.c_int32),
                 ("shard_count", C.c_int32), ("no_donation", C.c_int32), ("donate_every_iters", C.c_int32),
-                ("donate_every_us", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("donate_every_us", C.c_int32), ("domain_fixpoint", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class sge_result(C.Structure):
@@ -48,7 +49,9 @@ class sge_result(C.Structure):
                 ("preprocess_ms", C.c_double), ("match_ms", C.c_double), ("search_kernel_ms", C.c_double),
                 ("frames", C.c_int64), ("donations", C.c_int64), ("alg_bytes", C.c_uint64),
                 ("launches", C.c_int64), ("latency_ms", C.c_double), ("split_depth", C.c_int32),
-                ("status", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("status", C.c_int32), ("kernel", C.c_int32), ("split_kernel_ms", C.c_float),
+                ("queue_ms", C.c_float), ("split_exec_ms", C.c_float), ("search_exec_ms", C.c_float),
+                ("reserved", C.c_int32 * 1)]
 
 
 # numpy view of sge_result: batched calls write their results straight into such an array
@@ -136,7 +139,8 @@ def result_dict(r: sge_result) -> dict:
             "donations": int(r.donations), "alg_bytes": int(r.alg_bytes), "launches": int(r.launches),
             "latency_ms": float(r.latency_ms),
             "split_depth": int(r.split_depth), "status": int(r.status),
-            "kernel": int(r.kernel)}
+            "kernel": int(r.kernel), "split_kernel_ms": float(r.split_kernel_ms), "queue_ms": float(r.queue_ms),
+            "split_exec_ms": float(r.split_exec_ms), "search_exec_ms": float(r.search_exec_ms)}
 
 
 # ----------------------------------------------------------- C-named calls
@@ -333,10 +337,26 @@ def sge_cancel(ctx) -> None:
 
 # ------------------------------------------------------------- convenience
 class Context:
-    """Owns one engine context (and with it all device memory of its graphs)."""
+    """Owns one engine context (and with it all device memory of its graphs).
 
-    def __init__(self, device: int = 0, stream=None):
+    ``count_batch`` runs a batch with the schedule tuned for its workload class
+    (see ``autotune``) unless the call sets a schedule option or passes
+    ``tuned=False``; ``autotune_cache`` names the user cache consulted before the
+    one shipped with the package (None: only the package cache)."""
+
+    def __init__(self, device: int = 0, stream=None, autotune_cache: str | None = None):
+        from . import autotune
         self.h = sge_create(device, stream)
+        self.device = device
+        self.stream = stream
+        self.autotune_cache = autotune_cache if autotune_cache is not None else autotune.DEFAULT_PATH
+        # per loaded graph, indexed by its id (ids count up from 0 per context): vertices,
+        # edge labels present, directed -- the inputs of a batch's workload class
+        self._tn = np.zeros(0, np.int64)
+        self._tfl = np.zeros(0, np.int8)     # bit 0: edge-labelled, bit 1: directed
+        self._pk = np.zeros(0, np.int64)
+        self._pfl = np.zeros(0, np.int8)
+        self._tuned = {}      # workload class -> schedule options (looked up once)
 
     def close(self):
         if self.h:
@@ -355,16 +375,83 @@ class Context:
         except Exception:
             pass
 
+    @staticmethod
+    def _put(arr, i: int, v):
+        if i >= arr.shape[0]:
+            arr = np.concatenate([arr, np.zeros(max(i + 1 - arr.shape[0], arr.shape[0], 64), arr.dtype)])
+        arr[i] = v
+        return arr
+
     def load_target(self, g) -> int:
-        return sge_load_target(self.h, g.n, g.src, g.dst, g.vlabel, g.elabel, g.directed)
+        tid = sge_load_target(self.h, g.n, g.src, g.dst, g.vlabel, g.elabel, g.directed)
+        lab = g.elabel is not None and bool(np.any(np.asarray(g.elabel)))
+        self._tn = self._put(self._tn, tid, int(g.n))
+        self._tfl = self._put(self._tfl, tid, int(lab) | (2 if g.directed else 0))
+        return tid
 
     def load_pattern(self, g) -> int:
-        return sge_load_pattern(self.h, g.n, g.src, g.dst, g.vlabel, g.elabel, g.directed)
+        pid = sge_load_pattern(self.h, g.n, g.src, g.dst, g.vlabel, g.elabel, g.directed)
+        lab = g.elabel is not None and bool(np.any(np.asarray(g.elabel)))
+        self._pk = self._put(self._pk, pid, int(g.n))
+        self._pfl = self._put(self._pfl, pid, int(lab))
+        return pid
+
+    def synchronize(self):
+        """Wait for all device work (every engine call already returns with its own work done;
+        this also covers work the caller queued with PyTorch)."""
+        try:
+            import torch
+            torch.cuda.synchronize(self.device)
+        except Exception:
+            pass
+
+    def batch_key(self, tids, pids, algo: int = 0) -> str:
+        """Workload class of a batch (see autotune.batch_key).  The last batch's class is
+        remembered, so a caller that submits the same id arrays again pays nothing."""
+        ident = (id(tids), id(pids), len(tids), len(pids), int(algo))
+        last = getattr(self, "_last_key", None)
+        if last is not None and last[0] == ident:
+            return last[1]
+        key = self._batch_key(tids, pids, algo)
+        self._last_key = (ident, key)
+        return key
+
+    def _batch_key(self, tids, pids, algo: int = 0) -> str:
+        from . import autotune
+        t = np.asarray(tids)
+        p = np.asarray(pids)
+        if t.dtype.kind not in "iu":
+            t = t.astype(np.int64)
+        if p.dtype.kind not in "iu":
+            p = p.astype(np.int64)
+        if t.size == 0 or t.max() >= self._tn.shape[0] or p.max() >= self._pk.shape[0] or t.min() < 0 or p.min() < 0:
+            return autotune.batch_key(int(algo), 0, 0, int(t.size))    # ids this context did not load
+        # a batch's targets and patterns are usually few distinct graphs repeated: reduce over
+        # the per-id tables restricted to the ids present
+        tpres = np.zeros(self._tn.shape[0], bool)
+        tpres[t] = True
+        ppres = np.zeros(self._pk.shape[0], bool)
+        ppres[p] = True
+        tf = np.bitwise_or.reduce(self._tfl[tpres]) if tpres.any() else 0
+        pf = np.bitwise_or.reduce(self._pfl[ppres]) if ppres.any() else 0
+        return autotune.batch_key(int(algo), int(self._tn[tpres].max()), int(self._pk[ppres].max()), int(t.size),
+                                  bool((tf | pf) & 1), bool(tf & 2))
+
+    def tuned_schedule(self, tids, pids, algo: int = 0) -> dict:
+        """Schedule options tuned for this batch's workload class ({} if none)."""
+        from . import autotune
+        key = self.batch_key(tids, pids, algo)
+        if key not in self._tuned:
+            self._tuned[key] = autotune.lookup(key, self.autotune_cache, package=True)
+        return dict(self._tuned[key])
 
     def count(self, tid, pid, check=True, **opts) -> dict:
         return sge_count(self.h, tid, pid, make_opts(**opts), check=check)
 
-    def count_batch(self, tids, pids, check=True, **opts):
+    def count_batch(self, tids, pids, check=True, tuned=True, **opts):
+        from . import autotune
+        if tuned and not (set(opts) & autotune.SCHEDULE_KEYS):
+            opts = {**self.tuned_schedule(tids, pids, opts.get("algo", 0)), **opts}
         return sge_count_batch(self.h, tids, pids, make_opts(**opts), check=check)
 
     def count_batch_ckpt(self, tids, pids, check=True, **opts):

@@ -40,6 +40,8 @@ constexpr long long FRONTIER_MAX_INTS = 1ll << 27;  // 512 MB per frontier buffe
 constexpr int POOL_CELLS = 1 << 15;
 constexpr long long CAND_MAX = 1ll << 28;   // most listed domain candidates per launch group (1 GiB)
 constexpr int ROOT_CHUNK = 1024;                 // root candidates per root range frame
+constexpr int BLOCK_FIXPOINT_MAX_N = 16384;      // auto domain mode: in-block fixpoint for targets up to this
+constexpr long long LABEL_TABLE_MAX = 1ll << 26; // most (vertex, label) entries of a target's degree table
 
 // Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
 // SGE_TRACE: unset or "0" off; "errors" prints only failures; anything else
@@ -106,10 +108,30 @@ struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
     BlockCache *cache = nullptr;   // where released blocks go (null: cudaFree)
+    // Stream-ordered mode (launch-group workspaces, each used on one stream): blocks come from
+    // and go back to the device's memory pool in the order of `astream` (cudaMallocAsync /
+    // cudaFreeAsync), so growing a buffer never synchronises the device -- with several serving
+    // groups in flight, a cudaFree waited for every other group's kernels -- and a buffer grows
+    // by at least half its size at a time.
+    cudaStream_t astream = nullptr;
+    bool async = false;
     cudaError_t ensure(size_t bytes) {
         if (bytes <= cap && p) return cudaSuccess;
-        release();
         size_t nb = bytes < 256 ? 256 : bytes;
+        if (async) {
+            if (nb < cap + cap / 2) nb = cap + cap / 2;
+            release();
+            cudaError_t e = cudaMallocAsync(&p, nb, astream);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                nb = bytes < 256 ? 256 : bytes;   // retry at the exact size
+                e = cudaMallocAsync(&p, nb, astream);
+            }
+            if (e != cudaSuccess) { p = nullptr; cap = 0; return e; }
+            cap = nb;
+            return cudaSuccess;
+        }
+        release();
         if (cache) {
             size_t c = 0;
             if (void *q = cache->take(nb, &c)) {
@@ -129,11 +151,22 @@ struct DevBuf {
     }
     void release() {
         if (p) {
-            if (cache) cache->give(p, cap);
+            if (async) cudaFreeAsync(p, astream);
+            else if (cache) cache->give(p, cap);
             else cudaFree(p);
         }
         p = nullptr;
         cap = 0;
+    }
+    // Free at once, whatever the mode (the owner is going away, its stream perhaps with it).
+    void free_now() {
+        if (p) {
+            if (async && astream) cudaStreamSynchronize(astream);
+            cudaFree(p);
+        }
+        p = nullptr;
+        cap = 0;
+        async = false;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
@@ -243,6 +276,8 @@ struct TargetRec {
     long long nnz = 0;
     TargetView cached{};   // view(), taken once the record is complete
     DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj, hub_slot, hub_bits, hub_list;
+    DevBuf ltab;           // distinct labels, then the per-(vertex, label) largest neighbour degree
+    int nlab = 0, ltab_off = 0;
     TargetView view() const {
         TargetView v;
         v.n = n;
@@ -259,16 +294,20 @@ struct TargetRec {
         v.adj = adj.p ? adj.as<uint64_t>() : nullptr;
         v.hub_slot = hub_slot.p ? hub_slot.as<int32_t>() : nullptr;
         v.hub_bits = hub_bits.p ? hub_bits.as<uint64_t>() : nullptr;
+        v.labs = ltab.p ? ltab.as<int32_t>() : nullptr;
+        v.nbmax = ltab.p ? ltab.as<int32_t>() + ltab_off : nullptr;
+        v.nlab = ltab.p ? nlab : 0;
+        v.pad = 0;
         return v;
     }
     void use_cache(BlockCache *c) {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
-                          &hub_list})
+                          &hub_list, &ltab})
             b->cache = c;
     }
     void release() {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
-                          &hub_list})
+                          &hub_list, &ltab})
             b->release();
     }
     ~TargetRec() { release(); }
@@ -331,15 +370,29 @@ struct Workspace {
     DevBuf pool, pseq, ctl, slab;
     DevBuf mbuf, ckpt, wtrace, smask;
     std::vector<JobDesc> hdesc;   // host job records, reused
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;   // search kernel, split kernel
+    cudaStream_t bound = nullptr;
+#define SGE_WS_BUFFERS                                                                                             \
+    &jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag, &dent, &deoff, &vchg, \
+        &cand, &ctask, &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, \
+        &mbuf, &ckpt, &wtrace, &smask
+    // Every buffer of this workspace is used on `st` only: allocate them stream-ordered there.
+    void bind(cudaStream_t st) {
+        if (bound == st && st != nullptr) return;
+        for (DevBuf *b : {SGE_WS_BUFFERS}) {
+            if (b->p && b->async && b->astream != st) b->free_now();   // a block of another stream
+            b->async = true;
+            b->astream = st;
+        }
+        bound = st;
+    }
     void release() {
-        for (DevBuf *b : {&jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag,
-                          &dent, &deoff, &vchg, &cand, &ctask,
-                          &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, &mbuf, &ckpt, &wtrace, &smask})
-            b->release();
-        if (ev0) cudaEventDestroy(ev0);
-        if (ev1) cudaEventDestroy(ev1);
-        ev0 = ev1 = nullptr;
+        for (DevBuf *b : {SGE_WS_BUFFERS}) b->free_now();
+#undef SGE_WS_BUFFERS
+        bound = nullptr;
+        for (cudaEvent_t *e : {&ev0, &ev1, &ev2, &ev3})
+            if (*e) cudaEventDestroy(*e);
+        ev0 = ev1 = ev2 = ev3 = nullptr;
     }
 };
 
@@ -601,6 +654,13 @@ void parallel_for(int n, F body) {
     for (auto &x : th) x.join();
 }
 
+// Kernel span in ms from the words its blocks leave: ~(earliest start), latest end.
+float span_ms(unsigned long long inv_start, unsigned long long end) {
+    if (inv_start == 0 || end == 0) return 0.f;
+    const unsigned long long start = ~inv_start;
+    return end > start ? (float)((double)(end - start) * 1e-6) : 0.f;
+}
+
 int pow2_at_least(int x) {
     int p = 1;
     while (p < x) p <<= 1;
@@ -622,6 +682,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                      const Resume *resume = nullptr, std::vector<int32_t> *ckpt_frames = nullptr,
                      int *ckpt_kmax = nullptr) {
     const double t_start = now_ms();
+    W.bind(st);
     if (ckpt_frames) ckpt_frames->clear();
     long long launches = 0;   // kernels launched by this call
     const int algo = o.algo;
@@ -733,7 +794,28 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             any_rids = any_rids || jobs[q].algo != SGE_RI;
             any_fc = any_fc || jobs[q].algo == SGE_RIDS_SI_FC;
         }
-        if (any_rids) {
+        // RI-DS jobs in the batch; with many of them (or on request) the whole
+        // fixpoint of each job runs inside one block of one launch, else under the host loop
+        // below, whose sweeps spread one job's candidates over the whole device
+        // (the blocks scan domains word by word, which pays on small targets; large targets'
+        // domains are mostly empty words, which the candidate lists of the sweeps skip)
+        int nrids = 0;
+        bool small_targets = true;
+        for (int q : fjobs) {
+            nrids += jobs[q].algo != SGE_RI ? 1 : 0;
+            small_targets = small_targets && jobs[q].t->n <= BLOCK_FIXPOINT_MAX_N;
+        }
+        const bool block_fixpoint = any_rids && (o.domain_fixpoint == SGE_DOMAIN_BLOCKS ||
+                                                 (o.domain_fixpoint == SGE_DOMAIN_AUTO && nrids >= ctx->sms / 2 &&
+                                                  small_targets));
+        if (block_fixpoint) {
+            CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, st), "domain fixpoint");
+            ++launches;
+            if (trace_on()) {
+                CK(cudaStreamSynchronize(st), "fixpoint sync");
+                std::fprintf(stderr, "[sge] domain fixpoint in blocks: %d jobs at %.3f ms\n", nf, now_ms() - t_start);
+            }
+        } else if (any_rids) {
             // arc consistency to its fixpoint, alternating with forward checking.  A sweep
             // re-checks D(v) only if the domain of a pattern neighbour of v shrank in the
             // previous sweep (the first sweep of a round checks every RI-DS vertex).
@@ -993,6 +1075,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     }
     long long F0 = (long long)roots.size();
     long long F = 0;
+    float split_ms = 0.f;   // device time of the cooperative split (CUDA events)
+    float split_exec_ms = 0.f, search_exec_ms = 0.f;   // the kernels' own spans (device clock)
     int cur = 0, depth = 0, fstride = FRAME_HDR;
     bool split_done = F0 == 0;
     if (resume != nullptr) {
@@ -1035,6 +1119,11 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         constexpr long long SPLIT_MASKS = 1ll << 24;   // 64 MiB of replayed candidate ballots
         const bool have_masks = W.smask.ensure((size_t)SPLIT_MASKS * 4) == cudaSuccess;
         if (!have_masks) (void)cudaGetLastError();   // without the buffer the write pass tests again
+        if (!W.ev2) {
+            CK(cudaEventCreate(&W.ev2), "event");
+            CK(cudaEventCreate(&W.ev3), "event");
+        }
+        CK(cudaEventRecord(W.ev2, st), "event record");
         const cudaError_t le = launch_split_coop(W.jobs.as<JobDesc>(), F0, W.front[0].as<int32_t>(),
                                                  W.front[1].as<int32_t>(), cap_ints, target, max_levels, wtot,
                                                  wcap, bar, res, sstat, count_ctr, directed ? 1 : 0,
@@ -1042,11 +1131,14 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                                                  SPLIT_MASKS, st);
         if (le == cudaSuccess) {
             ++launches;
-            long long r4[4] = {0, 0, 0, 0};
+            CK(cudaEventRecord(W.ev3, st), "event record");
+            long long r4[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             int ss = 0;
             CK(cudaMemcpyAsync(r4, res, sizeof(r4), cudaMemcpyDeviceToHost, st), "read split result");
             CK(cudaMemcpyAsync(&ss, sstat, sizeof(int), cudaMemcpyDeviceToHost, st), "read split status");
             CK(cudaStreamSynchronize(st), "split sync");
+            CK(cudaEventElapsedTime(&split_ms, W.ev2, W.ev3), "event time");
+            split_exec_ms = span_ms((unsigned long long)r4[6], (unsigned long long)r4[7]);
             if (ss != 0) return fail(ctx, SGE_ERR_CUDA, "device split barrier timed out");
             F = r4[0];
             cur = (int)r4[1];
@@ -1132,13 +1224,17 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         // donation cadence: a busy warp checks whether idle warps wait for work at most once
         // per this many iterations or this much device time.  Donating costs a few microseconds
         // (two fetch-and-adds and one cell write), so the bitset kernel checks every 50 us; the
-        // CSR kernel's searches are mostly finished by the breadth-first split and keep 500 us.
+        // CSR kernel's searches are mostly finished by the breadth-first split and keep 500 us,
+        // except in serving groups: every 20 us there, so that the frames a group's split left
+        // (its deepest, heaviest subtrees) are shared before idle warps leave.
         const bool bits_k = kernel == SGE_KERNEL_BITSET;
-        C.donate_iters = o.donate_every_iters > 0 ? o.donate_every_iters : (bits_k ? (1 << 30) : 1024);
-        C.donate_ns = (unsigned long long)(o.donate_every_us > 0 ? o.donate_every_us : (bits_k ? 50 : 500)) * 1000ull;
-        // serving groups: idle warps leave after 20 us so a group's tail frees block slots
-        // for the next group's kernels
-        C.idle_exit_ns = serving ? 20000ull : 0ull;
+        C.donate_iters = o.donate_every_iters > 0 ? o.donate_every_iters
+                         : (bits_k || serving ? (1 << 30) : 1024);
+        C.donate_ns = (unsigned long long)(o.donate_every_us > 0 ? o.donate_every_us
+                                           : (bits_k ? 50 : (serving ? 20 : 500))) * 1000ull;
+        // serving groups: a warp idle for 200 us (ten donation periods without a frame for it)
+        // leaves, so a group's tail frees block slots for the next group's kernels
+        C.idle_exit_ns = serving ? 200000ull : 0ull;
         if (!W.ev0) {
             CK(cudaEventCreate(&W.ev0), "event");
             CK(cudaEventCreate(&W.ev1), "event");
@@ -1174,11 +1270,13 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                          st), "search launch");
         ++launches;
         CK(cudaEventRecord(W.ev1, st), "event record");
-        unsigned long long dn = 0;
+        unsigned long long dn = 0, sp[2] = {0, 0};
         CK(cudaMemcpyAsync(&status, C.status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
         CK(cudaMemcpyAsync(&dn, C.donations, 8, cudaMemcpyDeviceToHost, st), "read donations");
+        CK(cudaMemcpyAsync(sp, C.span, sizeof(sp), cudaMemcpyDeviceToHost, st), "read kernel span");
         CK(cudaStreamSynchronize(st), "search sync");
         CK(cudaEventElapsedTime(&kernel_ms, W.ev0, W.ev1), "event time");
+        search_exec_ms = span_ms(sp[0], sp[1]);
         donations = (long long)dn;
         if (trace_on()) {
             std::fprintf(stderr, "[sge] search grid %d frames %lld kernel %.3f ms status %d donations %llu\n", grid,
@@ -1291,6 +1389,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         r.preprocess_ms = t_pre - t_start;
         r.match_ms = t_end - t_pre;
         r.search_kernel_ms = kernel_ms;
+        r.split_kernel_ms = split_ms;
+        r.split_exec_ms = split_exec_ms;
+        r.search_exec_ms = search_exec_ms;
         r.frames = F;
         r.donations = donations;
         r.alg_bytes = kernel == SGE_KERNEL_BITSET ? ctr[5 * (size_t)nj + q] : 12ull * r.states;
@@ -1328,6 +1429,8 @@ sge_status prepare_pairs(sge_ctx *ctx, std::vector<PairReq> &reqs, const sge_opt
     }
     if (o.algo < SGE_RI || o.algo > SGE_RIDS_SI_FC) return fail(ctx, SGE_ERR_ARG, "unknown algo");
     if (o.kernel < 0 || o.kernel > 2) return fail(ctx, SGE_ERR_ARG, "unknown kernel family");
+    if (o.domain_fixpoint < SGE_DOMAIN_AUTO || o.domain_fixpoint > SGE_DOMAIN_BLOCKS)
+        return fail(ctx, SGE_ERR_ARG, "unknown domain fixpoint mode");
     if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count))
         return fail(ctx, SGE_ERR_ARG, "shard index out of range");
     und.clear();
@@ -1620,6 +1723,16 @@ sge_status sge_create(sge_ctx **out, int32_t device, void *cuda_stream) {
     if (!ctx) return SGE_ERR_OOM;
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    {
+        // workspaces allocate stream-ordered from the device's default pool: let the pool keep
+        // what they free for their next growth instead of returning it at every synchronisation
+        cudaMemPool_t mp;
+        if (cudaDeviceGetDefaultMemPool(&mp, device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        (void)cudaGetLastError();
+    }
     if (cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -1745,6 +1858,28 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
     }
     CK(T->vld.ensure(nv * sizeof(int2)), "alloc vertex info");
     CK(launch_make_vld(T->rowptr.as<int32_t>(), I.vlab.as<int32_t>(), T->vld.as<int2>(), n, st), "vertex info");
+    if (!directed && n > 0) {
+        // the largest neighbour degree per (vertex, label): domain initialisation reads it to
+        // drop, at once, the candidates that have no neighbour able to carry some pattern edge
+        std::vector<int32_t> labs(vlabel, vlabel + n);
+        std::sort(labs.begin(), labs.end());
+        labs.erase(std::unique(labs.begin(), labs.end()), labs.end());
+        const long long L = (long long)labs.size();
+        if ((long long)n * L <= LABEL_TABLE_MAX) {
+            std::vector<int32_t> lidx((size_t)n);
+            for (int v = 0; v < n; ++v)
+                lidx[(size_t)v] = (int32_t)(std::lower_bound(labs.begin(), labs.end(), vlabel[v]) - labs.begin());
+            T->nlab = (int)L;
+            T->ltab_off = (int)((L + 3) & ~3LL);
+            CK(T->ltab.ensure(((size_t)T->ltab_off + (size_t)n * L) * 4), "alloc label table");
+            CK(cudaMemcpyAsync(T->ltab.p, labs.data(), (size_t)L * 4, cudaMemcpyHostToDevice, st), "upload labels");
+            CK(cudaMemcpyAsync(I.fill_out.p, lidx.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st),
+               "upload label indices");
+            CK(launch_label_nbmax(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), T->vld.as<int2>(),
+                                  I.fill_out.as<int32_t>(), n, (int)L, T->ltab.as<int32_t>() + T->ltab_off, st),
+               "label table");
+        }
+    }
     if (!directed && n > 0 && n <= BITSET_MAX_N) {
         CK(T->adj.ensure((size_t)n * T->dw * 8), "alloc adjacency bitset");
         CK(cudaMemsetAsync(T->adj.p, 0, (size_t)n * T->dw * 8, st), "clear adjacency bitset");
@@ -2222,6 +2357,7 @@ void serve_worker(sge_ctx *ctx) {
             ctx->sbytes_in_use += bytes;
             ctx->sinflight += (int)group.size();
         }
+        const double t_admit = now_ms();
         std::vector<PairReq> reqs;
         for (auto &r : group) reqs.push_back({r->tid, r->pid});
         std::vector<sge_result> res(group.size());
@@ -2234,6 +2370,7 @@ void serve_worker(sge_ctx *ctx) {
             for (size_t i = 0; i < group.size(); ++i) {
                 group[i]->res = res[i];
                 group[i]->res.latency_ms = t_done - group[i]->t_submit;
+                group[i]->res.queue_ms = (float)(t_admit - group[i]->t_submit);
                 if (rc != SGE_OK && res[i].status == 0) group[i]->res.status = rc;
                 group[i]->done = true;
             }

@@ -209,7 +209,29 @@ __global__ void __launch_bounds__(IB) k_ing_bits(const int32_t *rowptr, const in
         }
 }
 
+// Largest neighbour degree per (vertex, label): one warp per vertex, lanes over its row.
+__global__ void __launch_bounds__(IB) k_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld,
+                                                    const int32_t *lidx, int n, int nlab, int32_t *nbmax) {
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (blockIdx.x * (long long)IB + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * IB) >> 5;
+    for (long long v = w0; v < n; v += nw)
+        for (int e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
+            const int y = col[e];
+            atomicMax(nbmax + (size_t)v * nlab + lidx[y], vld[y].y);
+        }
+}
+
 }  // namespace
+
+cudaError_t launch_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld, const int32_t *lidx, int n,
+                               int nlab, int32_t *nbmax, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(nbmax, 0, (size_t)n * nlab * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_label_nbmax<<<blocks_for((long long)n * 32, IB), IB, 0, st>>>(rowptr, col, vld, lidx, n, nlab, nbmax);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ingest_count(const int32_t *src, const int32_t *dst, const int32_t *elab, long long m, int n,
                                 int directed, int32_t *cnt_out, int32_t *cnt_in, int *flags, cudaStream_t st) {

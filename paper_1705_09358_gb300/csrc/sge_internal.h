@@ -77,6 +77,13 @@ struct TargetView {
     const uint64_t *adj;        // adjacency bitset rows (undirected, small n) or null
     const int32_t *hub_slot;    // large undirected targets: bitset row of vertex v, or -1
     const uint64_t *hub_bits;   // hub rows, dw words each
+    // undirected targets: the distinct vertex labels (ascending, nlab of them) and, per vertex t
+    // and label index l, the largest degree among t's neighbours of that label (0: none), in
+    // nbmax[t * nlab + l]; null when not built (directed targets, or n x nlab above 2^26)
+    const int32_t *labs;
+    const int32_t *nbmax;
+    int32_t nlab;
+    int32_t pad;
 };
 
 struct PatternView {
@@ -139,6 +146,7 @@ struct SearchCtl {
     int32_t ckpt_stride;        // FRAME_HDR + kmax
     unsigned long long *ckpt_n; // frames dumped (may exceed ckpt_cap: then the dump is incomplete)
     unsigned long long *wtrace; // optional per-warp trace records of WTRACE_WORDS words (null: off)
+    unsigned long long *span;   // [2]: ~(first block's start), last warp's end (%globaltimer, atomicMax)
 };
 
 constexpr int WTRACE_WORDS = 16;   // words of one warp's trace record (see WarpClock)
@@ -148,7 +156,7 @@ constexpr int WTRACE_WORDS = 16;   // words of one warp's trace record (see Warp
 // warps update others with atomics, and sharing one line would queue every
 // update behind the polls.
 constexpr size_t CTL_LINE = 128;
-constexpr size_t CTL_BYTES = 8 * CTL_LINE;
+constexpr size_t CTL_BYTES = 9 * CTL_LINE;
 inline void bind_control(SearchCtl &C, void *block) {
     char *b = static_cast<char *>(block);
     C.fnext = reinterpret_cast<unsigned long long *>(b + 0 * CTL_LINE);
@@ -159,6 +167,7 @@ inline void bind_control(SearchCtl &C, void *block) {
     C.idle = reinterpret_cast<int *>(b + 5 * CTL_LINE);
     C.status = reinterpret_cast<int *>(b + 6 * CTL_LINE);
     C.promised = reinterpret_cast<int *>(b + 7 * CTL_LINE);
+    C.span = reinterpret_cast<unsigned long long *>(b + 8 * CTL_LINE);
 }
 
 // ------------------------------------------------------------ launchers
@@ -173,6 +182,9 @@ cudaError_t launch_domain_ac(const JobDesc *jobs, const int4 *ent, const long lo
                              int *changed, unsigned char *vchanged, cudaStream_t st);
 cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, const long long *sizes, int njobs,
                              int *changed, unsigned char *vchanged, cudaStream_t st);
+// Arc consistency and forward checking to their joint fixpoint, one block per
+// job (for batches of many jobs; no host round trips).
+cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, cudaStream_t st);
 cudaError_t launch_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
                                 long long nverts, long long *sizes, cudaStream_t st);
 cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert,
@@ -185,8 +197,9 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
                          int count_ctr, int directed, cudaStream_t st);
 // The whole split as one cooperative launch (see k_split_coop): frames of
 // level L have stride FRAME_HDR + L in buffers of cap_ints ints; result[4] =
-// {final frame count, final buffer 0/1, levels done, last level's child count};
-// wtot needs one entry per warp of the grid (at most wtot_cap).
+// {final frame count, final buffer 0/1, levels done, last level's child count, -, -,
+// ~(first block's start), last block's end} (device clock; the host zeroes all eight);
+// wtot needs one entry per block of the grid (at most wtot_cap).
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
@@ -233,5 +246,8 @@ cudaError_t launch_ingest_compact(const long long *off, const long long *uoff, c
 cudaError_t launch_ingest_degree(const int32_t *rowptr, int n, int32_t *deg, cudaStream_t st);
 cudaError_t launch_ingest_bits(const int32_t *rowptr, const int32_t *col, int n, int dw, uint64_t *bits,
                                cudaStream_t st);
+// nbmax[t * nlab + lidx[y]] = max deg(y) over the neighbours y of t (nbmax zeroed first).
+cudaError_t launch_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld, const int32_t *lidx, int n,
+                               int nlab, int32_t *nbmax, cudaStream_t st);
 
 }  // namespace sge

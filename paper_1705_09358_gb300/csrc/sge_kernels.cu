@@ -204,6 +204,12 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
     const long long local = u - unit_off[j];
     const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
     const int lab = J.p.lab[v], od = J.p.odeg[v], id = DIR ? J.p.ideg[v] : 0;
+    // RI-DS on an undirected target without edge labels: a candidate t also needs, for every
+    // pattern neighbour u of v, a neighbour of its own with u's label and at least u's degree.
+    // That is arc consistency's test against the domains as initialised, so dropping the
+    // failures here removes only candidates the first sweep would remove; their rows, which
+    // the sweep would scan to the end, are never read.
+    const bool nbcheck = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && !DIR && J.t.nbmax != nullptr;
     unsigned long long word = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -212,6 +218,20 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
         if (t < J.t.n) {
             const int2 x = __ldg(J.t.vld + t);
             ok = x.x == lab && x.y >= od && (!DIR || __ldg(J.t.indeg + t) >= id);
+        }
+        if (nbcheck && __any_sync(FULL, ok)) {
+            const int32_t *row = J.t.nbmax + (size_t)t * J.t.nlab;
+            for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) {
+                const int u = J.p.col[e];
+                const int lu = J.p.lab[u];
+                int lo = 0, hi = J.t.nlab;   // label index of lab(u) among the target's labels
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(J.t.labs + mid) < lu) lo = mid + 1; else hi = mid;
+                }
+                const bool has = lo < J.t.nlab && __ldg(J.t.labs + lo) == lu;
+                if (ok) ok = has && __ldg(row + lo) >= J.p.odeg[u];
+            }
         }
         word |= (unsigned long long)__ballot_sync(FULL, ok) << (32 * h);
     }
@@ -400,6 +420,134 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const 
     }
 }
 
+// Arc consistency alternating with forward checking to their joint fixpoint
+// (Section 4, Section 4.2), all of one job inside one block: no host round
+// trip between sweeps, so a batch of many small jobs costs one launch.  A
+// sweep re-checks D(v) only for the vertices whose pattern neighbours' domains
+// shrank in the previous sweep (all vertices first); when arc consistency
+// holds, one forward-checking round clears the element of every new singleton
+// from the other domains, and the loop goes on until neither changes anything.
+// Removals are monotone deletions, so this schedule reaches the same unique
+// greatest fixpoint as any other.  A forward-checking round that finds an
+// empty domain ends the job (it has no match).  Blocks stride over the jobs.
+__global__ void __launch_bounds__(BLOCK) k_domain_fixpoint(const JobDesc *jobs, int njobs) {
+    __shared__ unsigned char dirty[KMAX], chg[KMAX], done[KMAX];
+    __shared__ int dl[KMAX], size[KMAX], elem[KMAX], newu[KMAX];
+    __shared__ int nd, any, nnew, empty;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+        const JobDesc &J = jobs[jb];
+        if (J.filt == nullptr || !(J.flags & JOB_RIDS)) continue;
+        const bool DIR = (J.flags & JOB_DIRECTED) != 0, chk = (J.flags & JOB_ELAB) != 0;
+        const bool FC = (J.flags & JOB_FC) != 0;
+        const int k = J.k, dw = J.t.dw;
+        for (int v = tid; v < k; v += blockDim.x) { dirty[v] = 1; done[v] = 0; }
+        if (tid == 0) empty = 0;
+        __syncthreads();
+        for (;;) {
+            // ---- arc consistency over the dirty vertices, to its fixpoint
+            for (;;) {
+                if (tid == 0) { nd = 0; any = 0; }
+                __syncthreads();
+                for (int v = tid; v < k; v += blockDim.x) {
+                    chg[v] = 0;
+                    if (dirty[v]) { dl[atomicAdd(&nd, 1)] = v; dirty[v] = 0; }
+                }
+                __syncthreads();
+                const int n_d = nd;
+                if (n_d == 0) break;
+                const long long units = (long long)n_d * dw;
+                for (long long x = tid; x < units; x += blockDim.x) {
+                    const int i = (int)(x / dw), q = (int)(x - (long long)i * dw), v = dl[i];
+                    uint64_t *wp = J.filt + (size_t)v * dw + q;
+                    const uint64_t w0 = *wp;
+                    uint64_t keep = w0;
+                    for (uint64_t w = w0; w; w &= w - 1) {
+                        const int b = __ffsll((long long)w) - 1;
+                        if (!ac_supported(J, v, q * 64 + b, DIR, chk)) keep &= ~(1ull << b);
+                    }
+                    if (keep != w0) {
+                        atomicAnd((unsigned long long *)wp, keep);
+                        chg[v] = 1;
+                        any = 1;
+                    }
+                }
+                __syncthreads();
+                if (!any) break;
+                // the pattern neighbours of every shrunk domain are checked again
+                for (int v = tid; v < k; v += blockDim.x) {
+                    if (!chg[v]) continue;
+                    for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) dirty[J.p.col[e]] = 1;
+                    if (DIR)
+                        for (int e = J.p.irowptr[v]; e < J.p.irowptr[v + 1]; ++e) dirty[J.p.icol[e]] = 1;
+                }
+                __syncthreads();
+            }
+            if (!FC) break;
+            // ---- one forward-checking round: |D(v)| by warps, then the new singletons
+            for (int v = wid; v < k; v += nwarps) {
+                unsigned long long c = 0;
+                for (int q = lane; q < dw; q += 32) c += __popcll(J.filt[(size_t)v * dw + q]);
+                c = warp_sum(c);
+                if (lane == 0) {
+                    size[v] = (int)c;
+                    if (c == 0) empty = 1;
+                }
+            }
+            if (tid == 0) nnew = 0;
+            __syncthreads();
+            if (empty) break;   // an empty domain: no match, nothing more to prune
+            for (int v = tid; v < k; v += blockDim.x) {
+                chg[v] = 0;
+                if (size[v] == 1 && !done[v]) {
+                    done[v] = 1;
+                    newu[atomicAdd(&nnew, 1)] = v;
+                }
+            }
+            __syncthreads();
+            const int nn = nnew;
+            if (nn == 0) break;   // both fixpoints hold
+            for (int sgl = wid; sgl < nn; sgl += nwarps) {
+                const int u = newu[sgl];
+                int found = -1;
+                for (int q0 = 0; q0 < dw && found < 0; q0 += 32) {
+                    const int q = q0 + lane;
+                    const uint64_t w = q < dw ? J.filt[(size_t)u * dw + q] : 0ull;
+                    const unsigned bal = __ballot_sync(FULL, w != 0);
+                    if (bal) {
+                        const int L = __ffs(bal) - 1;
+                        const uint64_t wl = __shfl_sync(FULL, w, L);
+                        found = (q0 + L) * 64 + __ffsll((long long)wl) - 1;
+                    }
+                }
+                if (lane == 0) elem[u] = found;
+            }
+            if (tid == 0) any = 0;
+            __syncthreads();
+            for (int x = tid; x < nn * k; x += blockDim.x) {
+                const int u = newu[x / k], v = x % k, t = elem[u];
+                if (v == u || t < 0) continue;
+                unsigned long long *wp = reinterpret_cast<unsigned long long *>(J.filt + (size_t)v * dw + (t >> 6));
+                const unsigned long long bit = 1ull << (t & 63);
+                if (atomicAnd(wp, ~bit) & bit) {
+                    chg[v] = 1;
+                    any = 1;
+                }
+            }
+            __syncthreads();
+            if (!any) break;
+            for (int v = tid; v < k; v += blockDim.x) {
+                if (!chg[v]) continue;
+                for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) dirty[J.p.col[e]] = 1;
+                if (DIR)
+                    for (int e = J.p.irowptr[v]; e < J.p.irowptr[v + 1]; ++e) dirty[J.p.icol[e]] = 1;
+            }
+            __syncthreads();
+        }
+        __syncthreads();   // the shared arrays are reused by the next job
+    }
+}
+
 // |D(v)| for every (job, pattern vertex); one warp each.
 __global__ void __launch_bounds__(BLOCK) k_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
                                                         long long nverts, long long *sizes) {
@@ -583,7 +731,7 @@ struct SplitCtl {
     long long cap_ints;
     long long target;           // stop once the frontier has this many frames
     int max_levels;
-    long long *wtot;            // [warps]: children per warp, then the warps' exclusive offsets
+    long long *wtot;            // [blocks]: children per block, then the blocks' exclusive offsets
     unsigned *bar;              // [2]: barrier count, generation (zeroed by the host)
     long long *result;          // [4]: final frame count, final buffer (0/1), levels done, last total
     int *status;
@@ -673,12 +821,14 @@ template <bool DIR>
 __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long long f0, SplitCtl S) {
     __shared__ int Msh[WARPS_PER_BLOCK][KMAX];
     __shared__ long long carry;
+    __shared__ long long woff[WARPS_PER_BLOCK];   // a level's child offsets of this block's warps
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *M = Msh[wib];
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long F = f0, total = 0;
     int cur = 0, level = 0;
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(S.result + 6), ~globaltimer());
     const long long mcap = S.masks ? S.mask_total / nw : 0;
     uint32_t *wm = S.masks ? S.masks + w * mcap : nullptr;
     for (; level < S.max_levels; ++level) {
@@ -691,18 +841,29 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         long long mine = 0, mp = 0;
         for (long long f = lo; f < hi; ++f)
             mine += split_frame<DIR>(jobs, fin + f * sin, M, 0, fout, 0, sout, S.count_ctr, wm, mcap, mp);
-        if (lane == 0) S.wtot[w] = mine;
+        // children offsets: warps within the block here, blocks across the grid in block 0
+        if (lane == 0) woff[wib] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long acc = 0;
+            for (int i = 0; i < WARPS_PER_BLOCK; ++i) {
+                const long long x = woff[i];
+                woff[i] = acc;
+                acc += x;
+            }
+            S.wtot[blockIdx.x] = acc;
+        }
         grid_barrier(S.bar, S.bar + 1, S.status);
         if (blockIdx.x == 0) {
-            // exclusive scan of the per-warp counts (one block, chunk by chunk)
+            // exclusive scan of the per-block counts (one block, chunk by chunk)
             if (threadIdx.x == 0) carry = 0;
             __syncthreads();
-            for (long long b = 0; b < nw; b += BLOCK) {
+            for (long long b = 0; b < gridDim.x; b += BLOCK) {
                 const long long i = b + threadIdx.x;
-                const long long x = i < nw ? S.wtot[i] : 0;
+                const long long x = i < gridDim.x ? S.wtot[i] : 0;
                 long long tot;
                 const long long ex = block_excl_scan(x, &tot);
-                if (i < nw) S.wtot[i] = carry + ex;
+                if (i < gridDim.x) S.wtot[i] = carry + ex;
                 __syncthreads();
                 if (threadIdx.x == 0) carry += tot;
                 __syncthreads();
@@ -712,7 +873,7 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         grid_barrier(S.bar, S.bar + 1, S.status);
         total = *(volatile long long *)(S.result + 3);
         if (total * sout > S.cap_ints) break;   // the next level does not fit: keep this frontier
-        const long long out = *(volatile long long *)(S.wtot + w);
+        const long long out = *(volatile long long *)(S.wtot + blockIdx.x) + woff[wib];
         long long written = 0;
         mp = 0;
         for (long long f = lo; f < hi; ++f)
@@ -727,6 +888,7 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
         S.result[1] = cur;
         S.result[2] = level;
     }
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(S.result + 7), globaltimer());
 }
 
 // =================================================================== scan
@@ -1199,11 +1361,12 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
     Frame fr;
-    long long iter = 0, last_don_iter = 0;
+    unsigned iter = 0, last_don_iter = 0;
     unsigned long long last_check = 0, last_don_ns = 0, last_cancel = 0;
     int cur_job = -1;
     CsrJob B;
     WarpClock::begin(C);
+    if (threadIdx.x == 0) atomicMax(C.span, ~globaltimer());
     while (acquire_frame(C, M, fr, deadline)) {
         WarpClock::frame_in(C);
         const JobDesc &J = jobs[fr.job];
@@ -1226,7 +1389,10 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
         const int k = B.k, d0 = fr.depth;
         // a counted frame re-tests its range at level d0 without counting it again
         const int quiet = fr.counted ? d0 : -1;
-        unsigned long long st = 0, nd = 0, mt = 0, hs = 0;
+        unsigned long long st = 0, nd = 0, mt = 0, hs = 0;   // the frame's totals
+        // since the last fold (every 64 iterations): an iteration adds at most 32 nodes and a
+        // candidate list below 2^24 states (longer lists go straight to the 64-bit total)
+        unsigned st32 = 0, nd32 = 0, mt32 = 0;
         // set up level `l` (positions 0..l-1 assigned)
         auto setup = [&](int l, int beg, int endv) {
             const PosC p = tab[l];
@@ -1258,13 +1424,19 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
         int lvl = d0;
         bool stopped = false;
         for (;;) {
-            if (((++iter) & 7) == 0 && time_to_check(last_check)) {
+            if (((++iter) & 63) == 0) {
+                st += st32; nd += nd32; mt += mt32;
+                st32 = nd32 = mt32 = 0;
+            }
+            if ((iter & 7) == 0 && time_to_check(last_check)) {
                 if (C.budget > 0) {
+                    st += st32;
+                    st32 = 0;
                     if (lane == 0) atomicAdd(J.ctr + 1, st);
                     st = 0;
                 }
                 if (must_stop(C, J, st, deadline, last_check, last_cancel)) { stopped = true; break; }
-                if ((iter - last_don_iter >= C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
+                if ((iter - last_don_iter >= (unsigned)C.donate_iters || last_check - last_don_ns >= C.donate_ns) &&
                     donation_claim(C)) {
                     // donate the shallowest unexplored work: half of an unscanned
                     // range, else up to `gran` pending survivors as new search nodes
@@ -1314,7 +1486,10 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                     continue;
                 }
                 const int cnt = min(32, end - cur);
-                if (cur == 0 && lvl != quiet) st += (unsigned long long)L.len;
+                if (cur == 0 && lvl != quiet) {
+                    if (L.len < (1 << 24)) st32 += (unsigned)L.len;
+                    else st += (unsigned long long)L.len;
+                }
                 bool ok = false;
                 int c = -1;
                 if (lane < cnt) {
@@ -1323,9 +1498,9 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                     ok = csr_feasible<DIR>(B, p, lvl, c, (src && p.par >= 0) ? e : -1, M);
                 }
                 unsigned bal = __ballot_sync(FULL, ok);
-                if (lvl != quiet) nd += __popc(bal);
+                if (lvl != quiet) nd32 += __popc(bal);
                 if (lvl == k - 1) {
-                    mt += __popc(bal);
+                    mt32 += __popc(bal);
                     if (bal) {
                         // hash prefix sum_{t < lvl} g(mu_t, M_t), only when this chunk has matches
                         unsigned long long ps = 0;
@@ -1370,6 +1545,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
                 }
             }
         }
+        st += st32; nd += nd32; mt += mt32;
         hs = warp_sum(hs);
         if (lane == 0) {
             atomicAdd(J.ctr + 0, mt);
@@ -1383,6 +1559,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
         if (stopped) break;
     }
     WarpClock::finish(C);
+    if ((threadIdx.x & 31) == 0) atomicMax(C.span + 1, globaltimer());
 }
 
 // ================================================== search: bitset kernel
@@ -1395,15 +1572,18 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
 //
 // Per warp, registers hold the used-vertex bitset (lane l: words l + 32 w) and
 // shared memory holds M, a compact copy of the job's position table, and for
-// every level a list of up to list_cap(kmax) pending survivors; a level with
+// every level a list of up to BitsLayout<KM>::LCAP pending survivors; a level with
 // more survivors keeps its
 // bitset in the warp's slab of global scratch (`SearchCtl::slab`) instead.
 
 // Capacity of a level's survivor list in shared memory: 64 for patterns of up
 // to 32 vertices (measured fastest on the dense workload), 16 beyond so that
 // four blocks of eight warps still fit an SM.  (The length byte reserves 0xff.)
-__host__ __device__ __forceinline__ int list_cap(int kmax) { return kmax <= 32 ? 64 : 16; }
 constexpr uint8_t LIST_SPILLED = 0xff;
+
+// Pattern-size class of a bitset-kernel launch: its per-warp shared layout is
+// fixed at compile time for patterns of at most KM vertices.
+__host__ __device__ constexpr int bits_km(int kmax) { return kmax <= 32 ? 32 : (kmax <= 64 ? 64 : KMAX); }
 
 struct __align__(16) PosB {
     int16_t pv, par, bb, bc;  // pattern vertex, parent position, back edges [bb, bb + bc) other than
@@ -1416,17 +1596,28 @@ constexpr int32_t PREV_ADJ = 1 << 28;   // mu_{i-1} is adjacent to mu_i (as pare
 constexpr int32_t PREV_PAR = 1 << 29;   // ... and is its parent
 constexpr int32_t ABYTES_MASK = (1 << 28) - 1;
 
+// Per-warp shared memory of the bitset kernel, at offsets fixed by KM: the
+// position table (16-byte records), the frame's range (for checkpoints), M,
+// the survivor lists and their lengths, and the back-edge positions.
+template <int KM>
+struct BitsLayout {
+    static constexpr int LCAP = KM <= 32 ? 64 : 16;
+    static constexpr size_t TAB = 0;
+    static constexpr size_t FRANGE = TAB + (size_t)KM * 16;
+    static constexpr size_t MOFF = FRANGE + 8;
+    static constexpr size_t LST = MOFF + (size_t)KM * 4;
+    static constexpr size_t LCNT = LST + (size_t)KM * LCAP * 2;
+    static constexpr size_t TBACK = LCNT + (size_t)KM;
+    static constexpr size_t BYTES = (TBACK + (size_t)KM * (KM - 1) / 2 + 16 + 15) & ~(size_t)15;
+};
+
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
-    return round16((size_t)kmax * sizeof(PosB) +            // position table (16-byte aligned)
-                   8 +                                      // the frame's range (for checkpoints)
-                   (size_t)kmax * 4 +                       // M
-                   (size_t)kmax * list_cap(kmax) * 2 +      // survivor lists
-                   (size_t)kmax +                           // list lengths
-                   (size_t)kmax * (kmax - 1) / 2 + 16);     // back-edge positions
+    return bits_km(kmax) == 32 ? BitsLayout<32>::BYTES
+                               : (bits_km(kmax) == 64 ? BitsLayout<64>::BYTES : BitsLayout<KMAX>::BYTES);
 }
 
 __host__ __device__ __forceinline__ size_t bits_slab_words_per_warp(int kmax, int nwl) {
-    return (size_t)kmax * nwl * 32;
+    return (size_t)bits_km(kmax) * nwl * 32;
 }
 
 struct BitsJob {
@@ -1435,15 +1626,38 @@ struct BitsJob {
     int dw, k;
 };
 
+// One warp's state: its shared-memory block (offsets from BitsLayout<KM>) and
+// its slab of global scratch (level bitsets of more survivors than a list holds).
+template <int KM>
 struct BitsWarp {
-    int *M;
-    PosB *tab;
-    uint16_t *lst;     // [kmax][lcap]
-    int lcap;          // list_cap(kmax)
-    uint8_t *lcnt;     // [kmax]
-    uint8_t *tback;
-    int *frange;       // [2]: the current frame's candidate range
-    uint64_t *slab;    // global: [kmax][NWL * 32]
+    using L = BitsLayout<KM>;
+    static constexpr int LCAP = L::LCAP;
+    unsigned char *base;
+    uint64_t *slab;    // global: [KM][NWL * 32]
+    // Level l's list length (LIST_SPILLED: its survivors are a slab bitset).  Patterns of up
+    // to 32 vertices keep the lengths in a register, lane l holding level l's, so a pop
+    // reads it with one shuffle and writes it with one select, no shared-memory store or
+    // warp sync; larger ones keep them in shared memory.
+    int lcr;
+    __device__ __forceinline__ int lc(int l) const {
+        if constexpr (KM == 32) return __shfl_sync(FULL, lcr, l);
+        else return lcnt()[l];
+    }
+    __device__ __forceinline__ void set_lc(int l, int v) {
+        if constexpr (KM == 32) {
+            lcr = (threadIdx.x & 31) == l ? v : lcr;
+        } else {
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) lcnt()[l] = (uint8_t)v;
+            __syncwarp();
+        }
+    }
+    __device__ __forceinline__ PosB *tab() const { return reinterpret_cast<PosB *>(base + L::TAB); }
+    __device__ __forceinline__ int *frange() const { return reinterpret_cast<int *>(base + L::FRANGE); }
+    __device__ __forceinline__ int *M() const { return reinterpret_cast<int *>(base + L::MOFF); }
+    __device__ __forceinline__ uint16_t *lst() const { return reinterpret_cast<uint16_t *>(base + L::LST); }
+    __device__ __forceinline__ uint8_t *lcnt() const { return base + L::LCNT; }
+    __device__ __forceinline__ uint8_t *tback() const { return base + L::TBACK; }
 };
 
 template <int NWL>
@@ -1481,13 +1695,13 @@ __device__ __forceinline__ void and_row(const uint64_t *adj, int dw, int x, uint
 // position i - 1 are ANDed too (then `used` must hold M_{i-1} as well), which
 // gives the whole candidate set S_i.  `len` receives the raw candidate count
 // when it does not depend on M[i-1] (else 0).
-template <int NWL>
-__device__ __forceinline__ void bits_rows(const BitsJob &B, const BitsWarp &W, const PosB &p, int i, bool with_prev,
+template <int NWL, int KM>
+__device__ __forceinline__ void bits_rows(const BitsJob &B, const BitsWarp<KM> &W, const PosB &p, int i, bool with_prev,
                                           const uint64_t (&used)[NWL], uint64_t (&s)[NWL], int &len) {
     const int lane = threadIdx.x & 31;
     const int dw = B.dw;
     const uint64_t *F = B.filt + (size_t)p.pv * dw;
-    const int *M = W.M;
+    const int *M = W.M();
 #pragma unroll
     for (int w = 0; w < NWL; ++w) {
         const int q = lane + 32 * w;
@@ -1504,7 +1718,7 @@ __device__ __forceinline__ void bits_rows(const BitsJob &B, const BitsWarp &W, c
         }
     }
 #pragma unroll 2
-    for (int b = 0; b < p.bc; ++b) and_row<NWL>(B.adj, dw, M[W.tback[p.bb + b]], s);
+    for (int b = 0; b < p.bc; ++b) and_row<NWL>(B.adj, dw, M[W.tback()[p.bb + b]], s);
     if (with_prev && (p.abf & PREV_ADJ) && !(p.abf & PREV_PAR)) and_row<NWL>(B.adj, dw, M[i - 1], s);
 #pragma unroll
     for (int w = 0; w < NWL; ++w) s[w] &= ~used[w];
@@ -1518,8 +1732,8 @@ __device__ __forceinline__ void bits_rows(const BitsJob &B, const BitsWarp &W, c
 // (k_max + 1) x 128 x 8 bytes, and the caller folds them into 64-bit totals
 // every 64 expansions.  M[0..i-1] must be in shared memory when the set has
 // matches (the hash and the match rows read them).
-template <int NWL, bool RANGE = false>
-__device__ __forceinline__ int bits_finish(const JobDesc &J, const BitsWarp &W, uint64_t (&s)[NWL], int i, int pv,
+template <int NWL, int KM, bool RANGE = false>
+__device__ __forceinline__ int bits_finish(const JobDesc &J, BitsWarp<KM> &W, uint64_t (&s)[NWL], int i, int pv,
                                            bool leaf, unsigned long long &hs, int vlo = 0, int vhi = 0x7fffffff) {
     const int lane = threadIdx.x & 31;
     int cnt = 0;
@@ -1541,9 +1755,9 @@ __device__ __forceinline__ int bits_finish(const JobDesc &J, const BitsWarp &W, 
     if (total == 0) return 0;
     if (leaf) {
         // hash prefix sum_{t < i} g(mu_t, M_t), computed only when matches exist
-        const int *M = W.M;
+        const int *M = W.M();
         unsigned long long ps = 0;
-        for (int t = lane; t < i; t += 32) ps += gterm(W.tab[t].pv, M[t]);
+        for (int t = lane; t < i; t += 32) ps += gterm(W.tab()[t].pv, M[t]);
         ps = warp_sum(ps);
 #pragma unroll
         for (int w = 0; w < NWL; ++w) {
@@ -1559,14 +1773,14 @@ __device__ __forceinline__ int bits_finish(const JobDesc &J, const BitsWarp &W, 
         }
         return total;
     }
-    if (total <= W.lcap) {
+    if (total <= W.LCAP) {
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += y;
         }
-        uint16_t *L = W.lst + i * W.lcap;
+        uint16_t *L = W.lst() + i * W.LCAP;
         int o = incl - cnt;
 #pragma unroll
         for (int w = 0; w < NWL; ++w) {
@@ -1578,29 +1792,26 @@ __device__ __forceinline__ int bits_finish(const JobDesc &J, const BitsWarp &W, 
             }
         }
         __syncwarp();
-        if (lane == 0) W.lcnt[i] = (uint8_t)total;
+        W.set_lc(i, total);
     } else {
         uint64_t *Sl = W.slab + (size_t)i * NWL * 32;
 #pragma unroll
         for (int w = 0; w < NWL; ++w) Sl[w * 32 + lane] = s[w];
         __syncwarp();
-        if (lane == 0) W.lcnt[i] = LIST_SPILLED;
+        W.set_lc(i, LIST_SPILLED);
     }
-    __syncwarp();
     return total;
 }
 
 // Next pending survivor of level l (warp-uniform, -1 if none); removes it.
-template <int NWL>
-__device__ __forceinline__ int bits_next(const BitsWarp &W, int l) {
+template <int NWL, int KM>
+__device__ __forceinline__ int bits_next(BitsWarp<KM> &W, int l) {
     const int lane = threadIdx.x & 31;
-    const int c = W.lcnt[l];
+    const int c = W.lc(l);
     if (c != LIST_SPILLED) {
         if (c == 0) return -1;
-        const int v = W.lst[l * W.lcap + c - 1];
-        __syncwarp();
-        if (lane == 0) W.lcnt[l] = (uint8_t)(c - 1);
-        __syncwarp();
+        const int v = W.lst()[l * W.LCAP + c - 1];
+        W.set_lc(l, c - 1);
         return v;
     }
     uint64_t *S = W.slab + (size_t)l * NWL * 32;
@@ -1622,35 +1833,31 @@ __device__ __forceinline__ int bits_next(const BitsWarp &W, int l) {
 }
 
 // Put a survivor back at level l (the donation queue was full).
-template <int NWL>
-__device__ __forceinline__ void bits_unnext(const BitsWarp &W, int l, int v) {
+template <int NWL, int KM>
+__device__ __forceinline__ void bits_unnext(BitsWarp<KM> &W, int l, int v) {
     const int lane = threadIdx.x & 31;
-    const int c = W.lcnt[l];
+    const int c = W.lc(l);
     __syncwarp();
     if (c != LIST_SPILLED) {
-        if (lane == 0) { W.lst[l * W.lcap + c] = (uint16_t)v; W.lcnt[l] = (uint8_t)(c + 1); }
+        if (lane == 0) W.lst()[l * W.LCAP + c] = (uint16_t)v;
+        __syncwarp();
+        W.set_lc(l, c + 1);
     } else {
         const int q = v >> 6;
         if (lane == (q & 31)) W.slab[(size_t)l * NWL * 32 + (q >> 5) * 32 + lane] |= 1ull << (v & 63);
+        __syncwarp();
     }
-    __syncwarp();
 }
 
-template <int NWL>
+template <int NWL, int KM>
 __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, SearchCtl C, int kmax) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    unsigned char *base = smem + wib * bits_smem_per_warp(kmax, NWL);
-    BitsWarp W;
-    W.tab = reinterpret_cast<PosB *>(base);
-    W.frange = reinterpret_cast<int *>(W.tab + kmax);
-    W.M = W.frange + 2;
-    W.lst = reinterpret_cast<uint16_t *>(W.M + kmax);
-    W.lcap = list_cap(kmax);
-    W.lcnt = reinterpret_cast<uint8_t *>(W.lst + (size_t)kmax * W.lcap);
-    W.tback = W.lcnt + kmax;
-    W.slab = C.slab + ((size_t)blockIdx.x * WARPS_PER_BLOCK + wib) * bits_slab_words_per_warp(kmax, NWL);
-    int *M = W.M;
+    BitsWarp<KM> W;
+    W.base = smem + wib * BitsLayout<KM>::BYTES;
+    W.slab = C.slab + ((size_t)blockIdx.x * WARPS_PER_BLOCK + wib) * ((size_t)KM * NWL * 32);
+    W.lcr = 0;
+    int *M = W.M();
     uint64_t used[NWL];   // this lane's words of the used-vertex bitset (word lane + 32 w)
 
     const unsigned long long deadline = C.deadline_ns ? globaltimer() + C.deadline_ns : 0ull;
@@ -1660,6 +1867,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
     int cur_job = -1;
     BitsJob B;
     WarpClock::begin(C);
+    if (threadIdx.x == 0) atomicMax(C.span, ~globaltimer());
     while (acquire_frame(C, M, fr, deadline)) {
         WarpClock::frame_in(C);
         const JobDesc &J = jobs[fr.job];
@@ -1678,11 +1886,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                 q.ucnt = (J.flags & JOB_RIDS) ? P.ucnt : J.t.n;   // RI: all of V_t
                 q.abf = ((P.par >= 0 ? 2 : 1) + P.bcnt) * J.t.dw * 8 | (prev_back || prev_par ? PREV_ADJ : 0) |
                         (prev_par ? PREV_PAR : 0);
-                W.tab[t] = q;
+                W.tab()[t] = q;
             }
             __syncwarp();
             const int nb = J.pos[B.k - 1].bbeg + J.pos[B.k - 1].bcnt;
-            for (int b = lane; b < nb; b += 32) W.tback[b] = (uint8_t)J.back[b].pos;
+            for (int b = lane; b < nb; b += 32) W.tback()[b] = (uint8_t)J.back[b].pos;
             __syncwarp();
         }
         const int k = B.k, d0 = fr.depth;
@@ -1701,7 +1909,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         // lists are ascending, that is the vertex-id interval [first, last]
         int vlo = 0, vhi = 0x7fffffff;
         if (fr.beg >= 0) {
-            const PosB p = W.tab[d0];
+            const PosB p = W.tab()[d0];
             const int32_t *lst = nullptr;
             int b0 = 0, len = 0;
             if (p.par >= 0) {
@@ -1721,20 +1929,20 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             else if (lst) { vlo = __ldg(lst + b0 + fr.beg); vhi = __ldg(lst + b0 + e - 1); }
             else { vlo = fr.beg; vhi = e - 1; }
         }
-        if (lane == 0) { W.frange[0] = fr.beg; W.frange[1] = fr.end; }   // read back only by a checkpoint
+        if (lane == 0) { W.frange()[0] = fr.beg; W.frange()[1] = fr.end; }   // read back only by a checkpoint
         const bool count_len = fr.beg <= 0 && !fr.counted;
         const bool leaf0 = d0 == k - 1;
         int c0;
         {
             // the frame's first expansion: position d0 with M[0..d0-1] given and all in `used`
-            const PosB p = W.tab[d0];
+            const PosB p = W.tab()[d0];
             uint64_t s[NWL];
             int len;
-            bits_rows<NWL>(B, W, p, d0, true, used, s, len);
+            bits_rows<NWL, KM>(B, W, p, d0, true, used, s, len);
             if (count_len) st32 += (unsigned)len;
             ab32 += (unsigned)(p.abf & ABYTES_MASK);
-            c0 = fr.beg >= 0 ? bits_finish<NWL, true>(J, W, s, d0, p.pv, leaf0, hs, vlo, vhi)
-                             : bits_finish<NWL>(J, W, s, d0, p.pv, leaf0, hs);
+            c0 = fr.beg >= 0 ? bits_finish<NWL, KM, true>(J, W, s, d0, p.pv, leaf0, hs, vlo, vhi)
+                             : bits_finish<NWL, KM>(J, W, s, d0, p.pv, leaf0, hs);
         }
         if (!fr.counted) nd += c0;
         if (leaf0) {
@@ -1754,10 +1962,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
             for (int w = 0; w < NWL; ++w) Pv[w] = 0ull;
             for (;;) {
                 if (((++iter) & 63) == 0) {
-                    st += st32; nd += nd32; mt += mt32; ab += ab32;
-                    st32 = nd32 = mt32 = ab32 = 0;
-                }
-                if ((iter & 63) == 0 && time_to_check(last_check)) {
+                  st += st32; nd += nd32; mt += mt32; ab += ab32;
+                  st32 = nd32 = mt32 = ab32 = 0;
+                  if (time_to_check(last_check)) {
                     if (C.budget > 0) {
                         if (lane == 0) atomicAdd(J.ctr + 1, st);
                         st = 0;
@@ -1773,10 +1980,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         for (int l = d0; l <= lvl && l + 1 + DONATE_MIN_LEVELS <= k; ++l) {
                             given = 0;
                             while (given < C.gran) {
-                                const int v = bits_next<NWL>(W, l);
+                                const int v = bits_next<NWL, KM>(W, l);
                                 if (v < 0) break;
                                 if (!push_frame(C, fr.job, l + 1, -1, -1, M, l, v)) {
-                                    bits_unnext<NWL>(W, l, v);
+                                    bits_unnext<NWL, KM>(W, l, v);
                                     given = C.gran;
                                     break;
                                 }
@@ -1787,8 +1994,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         WarpClock::don_end(C, tdon, given);
                         donation_done(C);
                     }
+                  }
                 }
-                const int v = bits_next<NWL>(W, lvl);
+                const int v = bits_next<NWL, KM>(W, lvl);
                 if (v < 0) {
                     if (lvl == d0) break;
                     --lvl;
@@ -1797,9 +2005,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                     continue;
                 }
                 const int i = lvl + 1;
-                const PosB p = W.tab[i];
+                const PosB p = W.tab()[i];
                 if (!pok) {
-                    bits_rows<NWL>(B, W, p, i, false, used, Pv, plen);
+                    bits_rows<NWL, KM>(B, W, p, i, false, used, Pv, plen);
                     pok = true;
                 }
                 uint64_t s[NWL];
@@ -1830,11 +2038,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         if (lane == 0) M[lvl] = v;
                         __syncwarp();
                     }
-                    const int c = bits_finish<NWL>(J, W, s, i, p.pv, true, hs);
+                    const int c = bits_finish<NWL, KM>(J, W, s, i, p.pv, true, hs);
                     nd32 += c;
                     mt32 += c;
                 } else {
-                    const int c = bits_finish<NWL>(J, W, s, i, p.pv, false, hs);
+                    const int c = bits_finish<NWL, KM>(J, W, s, i, p.pv, false, hs);
                     nd32 += c;
                     if (c > 0) {
                         if (lane == 0) M[lvl] = v;
@@ -1842,7 +2050,17 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         used_flip<NWL>(used, v);
                         lvl = i;
                         pok = false;
+                        continue;
                     }
+                }
+                // no descent: when that was the last survivor of its list, go up at once
+                // (levels whose lists ran out) instead of finding out on the next iteration
+                if (lvl > d0 && W.lc(lvl) == 0) {
+                    do {
+                        --lvl;
+                        used_flip<NWL>(used, M[lvl]);
+                    } while (lvl > d0 && W.lc(lvl) == 0);
+                    pok = false;
                 }
             }
             if (stopped && C.ckpt != nullptr) {
@@ -1851,7 +2069,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                 // taken from its top, a spilled bitset from its lowest bit), so one index range
                 // of the level's candidate list holds exactly them among the feasible candidates.
                 for (int l = d0; l <= lvl; ++l) {
-                    const PosB p = W.tab[l];
+                    const PosB p = W.tab()[l];
                     const int32_t *lst = nullptr;
                     int len = J.t.n;
                     if (p.par >= 0) {
@@ -1864,14 +2082,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
                         len = J.pos[l].ucnt;
                     }
                     int lo = 0, hi = len;   // the level's own range
-                    if (l == d0 && W.frange[0] >= 0) { lo = W.frange[0]; hi = min(W.frange[1], len); }
-                    const int c = W.lcnt[l];
+                    if (l == d0 && W.frange()[0] >= 0) { lo = W.frange()[0]; hi = min(W.frange()[1], len); }
+                    const int c = W.lc(l);
                     if (c == 0) continue;
                     if (c != LIST_SPILLED) {
-                        const int vmax = W.lst[l * W.lcap + c - 1];
+                        const int vmax = W.lst()[l * W.LCAP + c - 1];
                         hi = lst ? lower_bound_warp(lst, len, vmax + 1) : vmax + 1;
                     } else {
-                        const int vmin = bits_next<NWL>(W, l);
+                        const int vmin = bits_next<NWL, KM>(W, l);
                         if (vmin < 0) continue;
                         lo = lst ? lower_bound_warp(lst, len, vmin) : vmin;
                     }
@@ -1894,6 +2112,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_search_bits(const JobDesc *jobs, S
         if (stopped) break;
     }
     WarpClock::finish(C);
+    if ((threadIdx.x & 31) == 0) atomicMax(C.span + 1, globaltimer());
 }
 
 unsigned grid_for(long long warps) {
@@ -1933,6 +2152,17 @@ cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, con
                              int *changed, unsigned char *vchanged, cudaStream_t st) {
     if (njobs <= 0) return cudaSuccess;
     k_domain_fc<<<njobs, BLOCK, 0, st>>>(jobs, vert_off, sizes, changed, vchanged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, cudaStream_t st) {
+    if (njobs <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = njobs < sms * 8 ? njobs : sms * 8;
+    k_domain_fixpoint<<<grid, BLOCK, 0, st>>>(jobs, njobs);
     return cudaGetLastError();
 }
 
@@ -2079,9 +2309,18 @@ cudaError_t search_blocks_per_sm(int kernel, int kmax, int nwl, int directed, in
     const size_t smem = search_smem_bytes(kernel, kmax, nwl);
     if (kernel == 2) {
         switch (nwl) {
-            case 1: return occupancy_of(k_search_bits<1>, smem, occ);
-            case 2: return occupancy_of(k_search_bits<2>, smem, occ);
-            case 4: return occupancy_of(k_search_bits<4>, smem, occ);
+            case 1:
+                return kmax <= 32 ? occupancy_of(k_search_bits<1, 32>, smem, occ)
+                       : kmax <= 64 ? occupancy_of(k_search_bits<1, 64>, smem, occ)
+                                    : occupancy_of(k_search_bits<1, KMAX>, smem, occ);
+            case 2:
+                return kmax <= 32 ? occupancy_of(k_search_bits<2, 32>, smem, occ)
+                       : kmax <= 64 ? occupancy_of(k_search_bits<2, 64>, smem, occ)
+                                    : occupancy_of(k_search_bits<2, KMAX>, smem, occ);
+            case 4:
+                return kmax <= 32 ? occupancy_of(k_search_bits<4, 32>, smem, occ)
+                       : kmax <= 64 ? occupancy_of(k_search_bits<4, 64>, smem, occ)
+                                    : occupancy_of(k_search_bits<4, KMAX>, smem, occ);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -2116,9 +2355,27 @@ cudaError_t launch_search(int kernel, const JobDesc *jobs, const SearchCtl &ctl,
     const size_t smem = search_smem_bytes(kernel, kmax, nwl);
     if (kernel == 2) {
         switch (nwl) {
-            case 1: return launch_persistent(k_search_bits<1>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
-            case 2: return launch_persistent(k_search_bits<2>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
-            case 4: return launch_persistent(k_search_bits<4>, jobs, ctl, kmax, smem, blocks_per_sm, max_grid, grid_out, st);
+            case 1:
+                return kmax <= 32 ? launch_persistent(k_search_bits<1, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                      max_grid, grid_out, st)
+                       : kmax <= 64 ? launch_persistent(k_search_bits<1, 64>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                        max_grid, grid_out, st)
+                                    : launch_persistent(k_search_bits<1, KMAX>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                        max_grid, grid_out, st);
+            case 2:
+                return kmax <= 32 ? launch_persistent(k_search_bits<2, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                      max_grid, grid_out, st)
+                       : kmax <= 64 ? launch_persistent(k_search_bits<2, 64>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                        max_grid, grid_out, st)
+                                    : launch_persistent(k_search_bits<2, KMAX>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                        max_grid, grid_out, st);
+            case 4:
+                return kmax <= 32 ? launch_persistent(k_search_bits<4, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                      max_grid, grid_out, st)
+                       : kmax <= 64 ? launch_persistent(k_search_bits<4, 64>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                        max_grid, grid_out, st)
+                                    : launch_persistent(k_search_bits<4, KMAX>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                        max_grid, grid_out, st);
             default: return cudaErrorInvalidValue;
         }
     }
