@@ -654,6 +654,13 @@ void parallel_for(int n, F body) {
     for (auto &x : th) x.join();
 }
 
+// With SGE_TRACE=1: wait for the stream and print when a phase of run_group ended.
+void trace_phase(cudaStream_t st, const char *what, double t_start) {
+    if (!trace_on()) return;
+    cudaStreamSynchronize(st);
+    std::fprintf(stderr, "[sge] phase %s done at %.3f ms\n", what, now_ms() - t_start);
+}
+
 // Kernel span in ms from the words its blocks leave: ~(earliest start), latest end.
 float span_ms(unsigned long long inv_start, unsigned long long end) {
     if (inv_start == 0 || end == 0) return 0.f;
@@ -787,8 +794,10 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         CK(upload(W.vert_off, vert_off, st), "upload vertex offsets");
         CK(W.sizes.ensure((size_t)nverts * 8), "alloc sizes");
         CK(W.flag.ensure(64), "alloc flag");
+        trace_phase(st, "domain uploads", t_start);
         CK(launch_domain_init(W.fjobs.as<JobDesc>(), W.unit_off.as<long long>(), nf, nunits, st), "domain init");
         ++launches;
+        trace_phase(st, "domain init", t_start);
         bool any_rids = false, any_fc = false;
         for (int q : fjobs) {
             any_rids = any_rids || jobs[q].algo != SGE_RI;
@@ -870,6 +879,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                 const int nt = (int)tj.size();
                 CK(launch_domain_lists(W.fjobs.as<JobDesc>(), W.ctask.as<int>(), W.ctask.as<int>() + nt,
                                        W.ctask.as<int>() + 2 * nt, nt, W.cand.as<int32_t>(), st), "candidate lists");
+                trace_phase(st, "candidate lists", t_start);
                 ++launches;
             }
             // the neighbours of every shrunk domain (vchg) are re-checked next
@@ -959,6 +969,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                     if (s == 0) J.active = false;   // an empty domain: no match, no search
         }
     }
+    trace_phase(st, "domains", t_start);
     // orderings and position tables; RI tables depend only on the pattern and
     // are shared by every job of that pattern (n_t of an unparented RI position
     // is read from the job's target at run time)
@@ -1012,6 +1023,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                      "[sge] jobs %d kernel %d kmax %d nwl %d filt_words %lld: jobs %.3f, records %.3f, domains and "
                      "orders %.3f ms\n",
                      nj, kernel, kmax, nwl, filt_words, t_jobs - t_start, t_desc - t_jobs, now_ms() - t_desc);
+    trace_phase(st, "orderings", t_start);
     CK(upload(W.pos, pos, st), "upload positions");
     CK(upload(W.back, back, st), "upload back edges");
     CK(W.ulist.ensure((size_t)std::max<long long>(ulist_len, 1) * 4), "alloc lists");

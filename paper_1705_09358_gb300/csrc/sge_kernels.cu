@@ -268,28 +268,92 @@ __device__ bool ac_supported(const JobDesc &J, int v, int t, bool DIR, bool chk)
     return true;
 }
 
-// The same sweep over explicit candidate lists: one thread per listed
-// candidate of the listed entries {job, pattern vertex, global vertex,
-// list start}; a removed candidate is cleared from D(v) and its list slot.
+// Warp-collective form of ac_supported for a candidate with a long row: for each
+// pattern edge the 32 lanes stride t's row and a ballot says whether any of them
+// found a compatible neighbour in the other endpoint's domain.
+__device__ bool ac_supported_warp(const JobDesc &J, int v, int t, bool DIR, bool chk) {
+    const int lane = threadIdx.x & 31;
+    const int dw = J.t.dw;
+    for (int pass = 0; pass < (DIR ? 2 : 1); ++pass) {
+        const int32_t *prow = pass ? J.p.irowptr : J.p.rowptr;
+        const int32_t *pcol = pass ? J.p.icol : J.p.col;
+        const int32_t *pel = pass ? J.p.ielab : J.p.elab;
+        const int32_t *trow = pass ? J.t.irowptr : J.t.rowptr;
+        const int32_t *tcol = pass ? J.t.icol : J.t.col;
+        const int32_t *tel = pass ? J.t.ielab : J.t.elab;
+        const int fb = __ldg(trow + t), fe = __ldg(trow + t + 1);
+        for (int e = prow[v]; e < prow[v + 1]; ++e) {
+            const int uu = pcol[e], bl = chk ? pel[e] : 0;
+            const uint64_t *Du = J.filt + (size_t)uu * dw;
+            bool found = false;
+            for (int f0 = fb; f0 < fe && !found; f0 += 32) {
+                const int f = f0 + lane;
+                bool ok = false;
+                if (f < fe) {
+                    const int y = __ldg(tcol + f);
+                    ok = (!chk || __ldg(tel + f) == bl) && ((Du[y >> 6] >> (y & 63)) & 1ull);
+                }
+                found = __any_sync(FULL, ok);
+            }
+            if (!found) return false;
+        }
+    }
+    return true;
+}
+
+// Rows longer than this are searched by the whole warp (ac_supported_warp).
+constexpr int AC_WARP_ROW = 48;
+
+// The same sweep over explicit candidate lists: one lane per listed candidate of
+// the listed entries {job, pattern vertex, global vertex, list start}; a removed
+// candidate is cleared from D(v) and its list slot.  A lane tests a candidate with
+// a short row itself; the warp then takes its lanes' long-row candidates one at a
+// time together, so a hub's row is read 32 entries per step instead of one.
 __global__ void __launch_bounds__(BLOCK) k_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff,
                                                           int nent, long long ncand, int32_t *cand, int *changed,
                                                           unsigned char *vchanged) {
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= ncand) return;
-    const int i = find_job(eoff, nent, x);
-    const int4 E = ent[i];
-    const JobDesc &J = jobs[E.x];
-    int32_t *slot = cand + (long long)E.w + (x - eoff[i]);
-    const int t = *slot;
-    if (t < 0) return;
-    uint64_t *wp = J.filt + (size_t)E.y * J.t.dw + (t >> 6);
-    const uint64_t bit = 1ull << (t & 63);
-    if (!(*wp & bit)) { *slot = -1; return; }    // removed by forward checking
-    if (ac_supported(J, E.y, t, (J.flags & JOB_DIRECTED) != 0, (J.flags & JOB_ELAB) != 0)) return;
-    atomicAnd((unsigned long long *)wp, ~bit);
-    *slot = -1;
-    *changed = 1;
-    vchanged[E.z] = 1;
+    if ((x & ~31ll) >= ncand) return;   // warp-uniform: a warp with any candidate stays whole
+    const int lane = threadIdx.x & 31;
+    int jidx = 0, v = 0, g = 0, t = -1;
+    int32_t *slot = nullptr;
+    if (x < ncand) {
+        const int i = find_job(eoff, nent, x);
+        const int4 E = ent[i];
+        jidx = E.x; v = E.y; g = E.z;
+        slot = cand + (long long)E.w + (x - eoff[i]);
+        t = *slot;
+    }
+    bool drop = false, heavy = false;
+    if (t >= 0) {
+        const JobDesc &J = jobs[jidx];
+        uint64_t *wp = J.filt + (size_t)v * J.t.dw + (t >> 6);
+        if (!(*wp & (1ull << (t & 63)))) {
+            *slot = -1;                                  // removed by forward checking
+        } else {
+            const bool DIR = (J.flags & JOB_DIRECTED) != 0;
+            const int len = __ldg(J.t.rowptr + t + 1) - __ldg(J.t.rowptr + t) +
+                            (DIR ? __ldg(J.t.irowptr + t + 1) - __ldg(J.t.irowptr + t) : 0);
+            heavy = len > AC_WARP_ROW;
+            drop = !heavy && !ac_supported(J, v, t, DIR, (J.flags & JOB_ELAB) != 0);
+        }
+    }
+    unsigned hv = __ballot_sync(FULL, heavy);
+    while (hv) {
+        const int L = __ffs(hv) - 1;
+        hv &= hv - 1;
+        const int jl = __shfl_sync(FULL, jidx, L), vl = __shfl_sync(FULL, v, L), tl = __shfl_sync(FULL, t, L);
+        const JobDesc &J = jobs[jl];
+        const bool sup = ac_supported_warp(J, vl, tl, (J.flags & JOB_DIRECTED) != 0, (J.flags & JOB_ELAB) != 0);
+        if (lane == L) drop = !sup;
+    }
+    if (drop) {                                          // unsupported: remove t from D(v)
+        const JobDesc &J = jobs[jidx];
+        atomicAnd((unsigned long long *)(J.filt + (size_t)v * J.t.dw + (t >> 6)), ~(1ull << (t & 63)));
+        *slot = -1;
+        *changed = 1;
+        vchanged[g] = 1;
+    }
 }
 
 // One arc-consistency sweep (Section 4): drop t from D(v) when a pattern
