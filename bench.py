@@ -258,6 +258,7 @@ def search_roofline(kernel_s: float, alg_bytes: float, nodes: float, sm_mhz, sms
     hbm, hbm_kind = _peaks()
     rec = _measured_record()
     traffic = int(rec["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in rec else None
+    l2 = int(rec["lts_bytes_per_launch"]) if "lts_bytes_per_launch" in rec else None
     inst = int(rec["warp_instructions_per_launch"]) if "warp_instructions_per_launch" in rec else None
     mhz = float(sm_mhz) if sm_mhz else 2070.0
     peak = sms * WARP_SCHEDULERS_PER_SM * mhz * 1e6
@@ -271,6 +272,7 @@ def search_roofline(kernel_s: float, alg_bytes: float, nodes: float, sm_mhz, sms
                         f"{mhz:.0f} MHz (median SM clock in the timed region)",
            "frac_at_max_clock": inst / kernel_s / (sms * WARP_SCHEDULERS_PER_SM * 2070e6) if inst else None,
            "alg_bytes_per_launch": alg_bytes, "alg_bytes_gbs": alg_gbs, "alg_bytes_frac_of_hbm": alg_gbs / hbm,
+           "l2_bytes_per_launch": l2, "l2_gbs": l2 / kernel_s / 1e9 if l2 else None,
            "dram_gbs": traffic / kernel_s / 1e9 if traffic else None,
            "dram_frac_of_hbm": traffic / kernel_s / 1e9 / hbm if traffic else None,
            "hbm_peak_gbs": hbm, "hbm_peak_kind": f"of {hbm_kind} HBM copy"}
@@ -800,6 +802,36 @@ def _workload_pairs(E, name: str, cl100k_queries: int = 5000):
     raise ValueError(name)
 
 
+def run_workload(args):
+    """One named batched workload timed call by call (a profiling aid): `warmup`
+    untimed calls, then `steps` timed ones; one JSON line with the median call
+    time and the last call's phase times."""
+    import torch
+    import paper_1705_09358_gb300 as sge
+    sge.build.build()
+    E = sge.Context(0)
+    tids, pids, algo = _workload_pairs(E, args.workload, args.cl100k_queries)
+    if args.algo >= 0:
+        algo = args.algo
+    for _ in range(args.warmup):
+        E.count_batch(tids, pids, algo=algo)
+    times, rows = [], None
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, rows = E.count_batch(tids, pids, algo=algo)
+        times.append(time.perf_counter() - t0)
+    r0 = rows[0]
+    print(json.dumps({"workload": args.workload, "algo": algo, "pairs": len(pids),
+                      "seconds_median": float(np.median(times)), "seconds_min": min(times),
+                      "states": int(rows["states"].sum()), "matches": int(rows["matches"].sum()),
+                      "preprocess_ms": float(r0["preprocess_ms"]), "split_kernel_ms": float(r0["split_kernel_ms"]),
+                      "split_exec_ms": float(r0["split_exec_ms"]), "search_kernel_ms": float(r0["search_kernel_ms"]),
+                      "split_depth": int(r0["split_depth"]), "frames": int(r0["frames"]),
+                      "launches": int(r0["launches"])}), flush=True)
+    E.close()
+
+
 def run_tune(args):
     """Tune the schedule of each named workload (coordinate descent, whole-call time) and
     write the tuned points, keyed by workload class, to args.tune_out."""
@@ -834,7 +866,13 @@ def main():
     ap.add_argument("--tune", default="", help="comma-separated workloads to tune (er2000, cl10k, mol200, cl100k)")
     ap.add_argument("--tune-out", default=os.path.join(ROOT, "paper_1705_09358_gb300", "autotune_cache.json"))
     ap.add_argument("--cl100k-queries", type=int, default=5000)
+    ap.add_argument("--workload", default="",
+                    help="time one batched workload call by call (er2000, cl10k, cl10k-ri, mol200, cl100k)")
+    ap.add_argument("--algo", type=int, default=-1, help="with --workload: the variant (default: the workload's)")
     args = ap.parse_args()
+    if args.workload:
+        run_workload(args)
+        return
     if args.ablation:
         run_ablation(args)
         return

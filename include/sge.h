@@ -86,13 +86,18 @@ typedef struct {
     int32_t donate_every_us;   /* ... or once per this many microseconds, whichever comes first
                                   (defaults: CSR kernel 1024 / 500, bitset kernel 2^30 / 50) */
     int32_t domain_fixpoint;   /* RI-DS domains (arc consistency with forward checking, Section 4):
-                                  0 = auto (SGE_DOMAIN_BLOCKS when the batch holds at least half as
-                                  many RI-DS pairs as the device has SMs and every target has at
-                                  most 16384 vertices, else SGE_DOMAIN_SWEEPS),
                                   SGE_DOMAIN_SWEEPS = sweeps over the whole device under a host
-                                  loop, SGE_DOMAIN_BLOCKS = each pair's whole fixpoint in one block
-                                  of one launch; both reach the same fixpoint */
-    int32_t reserved[2];
+                                  loop; SGE_DOMAIN_BLOCKS = each pair's whole fixpoint in one block
+                                  of one launch (targets of at most 16384 vertices: word by word;
+                                  larger ones: over candidate lists); 0 = auto: blocks when the
+                                  batch holds at least half as many RI-DS pairs as the device has
+                                  SMs (small targets) or at least 32 (large targets), else sweeps.
+                                  All reach the same fixpoint. */
+    int32_t frontier_kib;      /* size of each of the breadth-first split's two frontier buffers
+                                  in KiB (default 524288 = 512 MiB); a split level whose children
+                                  do not fit is not taken, and the search starts from the
+                                  frontier as it stands */
+    int32_t reserved[1];
 } sge_opts;
 
 enum { SGE_DOMAIN_AUTO = 0, SGE_DOMAIN_SWEEPS = 1, SGE_DOMAIN_BLOCKS = 2 };

@@ -41,7 +41,8 @@ class sge_opts(C.Structure):
                 ("steal_granularity", C.c_int32), ("state_budget", C.c_int64), ("time_limit_ms", C.c_int64),
                 ("kernel", C.c_int32), ("blocks_per_sm", C.c_int32), ("shard_index", C.c_int32),
                 ("shard_count", C.c_int32), ("no_donation", C.c_int32), ("donate_every_iters", C.c_int32),
-                ("donate_every_us", C.c_int32), ("domain_fixpoint", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("donate_every_us", C.c_int32), ("domain_fixpoint", C.c_int32), ("frontier_kib", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class sge_result(C.Structure):

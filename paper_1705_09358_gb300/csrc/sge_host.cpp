@@ -42,6 +42,7 @@ constexpr long long CAND_MAX = 1ll << 28;   // most listed domain candidates per
 constexpr int ROOT_CHUNK = 1024;                 // root candidates per root range frame
 constexpr int BLOCK_FIXPOINT_MAX_N = 16384;      // auto domain mode: in-block fixpoint for targets up to this
 constexpr long long LABEL_TABLE_MAX = 1ll << 26; // most (vertex, label) entries of a target's degree table
+constexpr int LIST_FIXPOINT_MIN_JOBS = 32;      // auto domain mode: in-block fixpoint over lists from this many pairs
 
 // Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
 // SGE_TRACE: unset or "0" off; "errors" prints only failures; anything else
@@ -276,8 +277,10 @@ struct TargetRec {
     long long nnz = 0;
     TargetView cached{};   // view(), taken once the record is complete
     DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj, hub_slot, hub_bits, hub_list;
-    DevBuf ltab;           // distinct labels, then the per-(vertex, label) largest neighbour degree
+    DevBuf ltab;           // distinct labels, then the per-(label, vertex) largest neighbour degree
     int nlab = 0, ltab_off = 0;
+    std::vector<int32_t> labs_h;   // host copy of the distinct labels (ascending)
+    DevBuf lbk;            // large targets: label buckets (vertices, their degrees, bucket starts)
     TargetView view() const {
         TargetView v;
         v.n = n;
@@ -298,16 +301,19 @@ struct TargetRec {
         v.nbmax = ltab.p ? ltab.as<int32_t>() + ltab_off : nullptr;
         v.nlab = ltab.p ? nlab : 0;
         v.pad = 0;
+        v.lbuck = lbk.p ? lbk.as<int32_t>() : nullptr;
+        v.lbdeg = lbk.p ? lbk.as<int32_t>() + n : nullptr;
+        v.lbstart = lbk.p ? lbk.as<int32_t>() + 2 * (size_t)n : nullptr;
         return v;
     }
     void use_cache(BlockCache *c) {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
-                          &hub_list, &ltab})
+                          &hub_list, &ltab, &lbk})
             b->cache = c;
     }
     void release() {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
-                          &hub_list, &ltab})
+                          &hub_list, &ltab, &lbk})
             b->release();
     }
     ~TargetRec() { release(); }
@@ -368,14 +374,14 @@ struct Workspace {
         ctask;
     DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
-    DevBuf mbuf, ckpt, wtrace, smask;
+    DevBuf mbuf, ckpt, wtrace, smask, plidx, cstart;
     std::vector<JobDesc> hdesc;   // host job records, reused
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;   // search kernel, split kernel
     cudaStream_t bound = nullptr;
 #define SGE_WS_BUFFERS                                                                                             \
     &jobs, &fjobs, &ctr, &filt, &pos, &back, &ulist, &unit_off, &vert_off, &sizes, &task, &flag, &dent, &deoff, &vchg, \
         &cand, &ctask, &front[0], &front[1], &counts, &offs, &scan_tmp, &total, &splitctl, &pool, &pseq, &ctl, &slab, \
-        &mbuf, &ckpt, &wtrace, &smask
+        &mbuf, &ckpt, &wtrace, &smask, &plidx, &cstart
     // Every buffer of this workspace is used on `st` only: allocate them stream-ordered there.
     void bind(cudaStream_t st) {
         if (bound == st && st != nullptr) return;
@@ -633,13 +639,13 @@ struct PairReq {
     PatternRec *p = nullptr;
 };
 
-// Runs body(begin, end) over [0, n) split across a few host threads when n is
-// large (batches of many thousands of pairs), else inline.
+// Runs body(begin, end) over [0, n) split across up to 8 host threads, each with
+// at least `min_per_thread` items (16384 by default: batches of many thousands of
+// cheap pairs), else inline.
 template <class F>
-void parallel_for(int n, F body) {
-    constexpr int MIN_PER_THREAD = 16384;
+void parallel_for(int n, F body, int min_per_thread = 16384) {
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::min(std::min(8, hw), n / MIN_PER_THREAD);
+    const int nt = std::min(std::min(8, hw), n / min_per_thread);
     if (nt <= 1) {
         body(0, n);
         return;
@@ -762,6 +768,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             D.pos = nullptr;
             D.back = nullptr;
             D.ulist = nullptr;
+            D.plidx = nullptr;
             D.mbuf = nullptr;
             D.mcap = 0;
             D.k = J.p->k;
@@ -778,12 +785,36 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     std::vector<int> fjobs;  // jobs with a filter block, in order
     for (int q = 0; q < nj; ++q)
         if (jobs[q].active && jobs[q].filt_off >= 0) fjobs.push_back(q);
+    // RI-DS jobs on targets with a label-degree table (undirected, no edge labels in the batch):
+    // their pattern vertices' label indices among the target's labels, written on the device
+    // below into one array indexed like the domain sizes (job's vertex offset + vertex)
+    bool any_plidx = false;
+    if (!any_elab && !directed) {
+        long long g = 0;
+        for (int q : fjobs) {
+            const Job &J = jobs[q];
+            if (J.algo != SGE_RI && !J.t->labs_h.empty()) any_plidx = true;
+            g += J.p->k;
+        }
+        if (any_plidx) {
+            CK(W.plidx.ensure((size_t)std::max<long long>(g, 1) * 4), "alloc label indices");
+            g = 0;
+            for (int q : fjobs) {
+                const Job &J = jobs[q];
+                if (J.algo != SGE_RI && !J.t->labs_h.empty()) desc[q].plidx = W.plidx.as<int32_t>() + g;
+                g += J.p->k;
+            }
+        }
+    }
     std::vector<JobDesc> fdesc;
+    bool any_buckets = false;
     for (int q : fjobs) {
         unit_off.push_back(nunits);
         vert_off.push_back(nverts);
         jobs[q].vert_off = nverts;
-        nunits += (long long)jobs[q].p->k * jobs[q].t->dw;
+        // (targets with label buckets initialise their domains from the buckets, not word by word)
+        if (!jobs[q].t->lbk.p) nunits += (long long)jobs[q].p->k * jobs[q].t->dw;
+        else any_buckets = true;
         nverts += jobs[q].p->k;
         fdesc.push_back(desc[q]);
     }
@@ -792,11 +823,21 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         CK(upload(W.fjobs, fdesc, st), "upload domain jobs");
         CK(upload(W.unit_off, unit_off, st), "upload unit offsets");
         CK(upload(W.vert_off, vert_off, st), "upload vertex offsets");
+        if (any_plidx) {
+            CK(launch_label_index(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts, st), "label indices");
+            ++launches;
+        }
         CK(W.sizes.ensure((size_t)nverts * 8), "alloc sizes");
         CK(W.flag.ensure(64), "alloc flag");
         trace_phase(st, "domain uploads", t_start);
+        if (any_buckets) CK(cudaMemsetAsync(W.filt.p, 0, (size_t)filt_words * 8, st), "clear domains");
         CK(launch_domain_init(W.fjobs.as<JobDesc>(), W.unit_off.as<long long>(), nf, nunits, st), "domain init");
         ++launches;
+        if (any_buckets) {
+            CK(launch_domain_init_buckets(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts, st),
+               "domain init from buckets");
+            ++launches;
+        }
         trace_phase(st, "domain init", t_start);
         bool any_rids = false, any_fc = false;
         for (int q : fjobs) {
@@ -806,19 +847,20 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         // RI-DS jobs in the batch; with many of them (or on request) the whole
         // fixpoint of each job runs inside one block of one launch, else under the host loop
         // below, whose sweeps spread one job's candidates over the whole device
-        // (the blocks scan domains word by word, which pays on small targets; large targets'
-        // domains are mostly empty words, which the candidate lists of the sweeps skip)
+        // (on small targets the blocks scan domains word by word; large targets' domains are
+        // mostly empty words, so there the blocks walk candidate lists, built first, below)
         int nrids = 0;
         bool small_targets = true;
         for (int q : fjobs) {
             nrids += jobs[q].algo != SGE_RI ? 1 : 0;
             small_targets = small_targets && jobs[q].t->n <= BLOCK_FIXPOINT_MAX_N;
         }
-        const bool block_fixpoint = any_rids && (o.domain_fixpoint == SGE_DOMAIN_BLOCKS ||
-                                                 (o.domain_fixpoint == SGE_DOMAIN_AUTO && nrids >= ctx->sms / 2 &&
-                                                  small_targets));
+        const bool block_fixpoint = any_rids && small_targets &&
+                                    (o.domain_fixpoint == SGE_DOMAIN_BLOCKS ||
+                                     (o.domain_fixpoint == SGE_DOMAIN_AUTO && nrids >= ctx->sms / 2));
         if (block_fixpoint) {
-            CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, st), "domain fixpoint");
+            CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, nullptr, nullptr, nullptr, nullptr, st),
+               "domain fixpoint");
             ++launches;
             if (trace_on()) {
                 CK(cudaStreamSynchronize(st), "fixpoint sync");
@@ -882,6 +924,25 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                 trace_phase(st, "candidate lists", t_start);
                 ++launches;
             }
+            // many RI-DS pairs on large targets: each pair's whole fixpoint in one block, walking
+            // the candidate lists (no host round trip per sweep)
+            const bool list_blocks = cand_mode && (o.domain_fixpoint == SGE_DOMAIN_BLOCKS ||
+                                                   (o.domain_fixpoint == SGE_DOMAIN_AUTO && nrids >= LIST_FIXPOINT_MIN_JOBS));
+            if (list_blocks) {
+                std::vector<long long> cs((size_t)nverts * 2);
+                std::copy(cstart.begin(), cstart.end(), cs.begin());
+                std::copy(csize.begin(), csize.end(), cs.begin() + nverts);
+                CK(upload(W.cstart, cs, st), "upload candidate list offsets");
+                CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, W.vert_off.as<long long>(),
+                                          W.cstart.as<long long>(), W.cstart.as<long long>() + nverts,
+                                          W.cand.as<int32_t>(), st), "domain fixpoint");
+                ++launches;
+                if (trace_on()) {
+                    CK(cudaStreamSynchronize(st), "fixpoint sync");
+                    std::fprintf(stderr, "[sge] domain fixpoint over candidate lists in blocks: %d jobs at %.3f ms\n",
+                                 nf, now_ms() - t_start);
+                }
+            }
             // the neighbours of every shrunk domain (vchg) are re-checked next
             auto mark_neighbours = [&]() {
                 std::fill(dirty.begin(), dirty.end(), 0);
@@ -898,7 +959,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             std::vector<int4> ent;
             std::vector<long long> eoff;
             mark_all();
-            for (int outer = 0; outer < 100000; ++outer) {
+            for (int outer = 0; outer < (list_blocks ? 0 : 100000); ++outer) {
                 for (int sweep = 0; sweep < 1000000; ++sweep) {
                     ent.clear();
                     eoff.clear();
@@ -984,6 +1045,18 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     long long ulist_len = 0;
     std::vector<PosInfo> pq;
     std::vector<BackEdge> bq;
+    // the RI-DS jobs' orderings and tables (each depends on its own domain sizes) on a few host
+    // threads, into per-job vectors; they are appended in job order below
+    std::vector<std::vector<PosInfo>> jpos((size_t)nj);
+    std::vector<std::vector<BackEdge>> jback((size_t)nj);
+    parallel_for(nj, [&](int q0, int q1) {
+        for (int q = q0; q < q1; ++q) {
+            Job &J = jobs[q];
+            if (!J.active || J.algo == SGE_RI) continue;
+            gcf_order(*J.p, J.algo, J.dsize.data(), J.mu, J.par);
+            build_positions(*J.p, J.mu, J.par, J.algo, J.dsize.data(), J.t->n, jpos[(size_t)q], jback[(size_t)q]);
+        }
+    }, 64);
     for (int q = 0; q < nj; ++q) {
         Job &J = jobs[q];
         if (!J.active) continue;
@@ -1000,10 +1073,10 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             back_off[q] = it->second.second;
             continue;
         }
-        gcf_order(*J.p, J.algo, J.dsize.data(), J.mu, J.par);
         pos_off[q] = (long long)pos.size();
         back_off[q] = (long long)back.size();
-        build_positions(*J.p, J.mu, J.par, J.algo, J.dsize.data(), J.t->n, pq, bq);
+        std::vector<PosInfo> &pq = jpos[(size_t)q];
+        std::vector<BackEdge> &bq = jback[(size_t)q];
         for (PosInfo &p : pq) {
             if (p.par < 0) {
                 // the D(mu_i) list is written by a kernel below
@@ -1104,6 +1177,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         split_done = true;
     }
     const int max_levels = std::max(0, std::min(o.split_depth > 0 ? o.split_depth : INT_MAX, kmax - 1));
+    const long long front_ints = o.frontier_kib > 0 ? 256ll * o.frontier_kib : FRONTIER_MAX_INTS;
     if (!split_done && resume == nullptr) {
         // the whole split as one cooperative launch.  Auto depth, CSR kernel: breadth-first
         // for as long as the next level fits the frontier budget (deep, narrow searches are
@@ -1115,7 +1189,10 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         const bool limited = o.state_budget > 0 || o.time_limit_ms > 0;
         const long long target = o.split_depth > 0 ? LLONG_MAX
                                  : (kernel == SGE_KERNEL_BITSET || limited) ? target_frames : (long long)INT_MAX;
-        const long long cap_ints = std::max<long long>(F0 * FRAME_HDR, FRONTIER_MAX_INTS);
+        const long long cap_ints = std::max<long long>(F0 * FRAME_HDR, front_ints);
+        // sharded runs need the children in search order (frame i -> shard i mod S); an
+        // unsharded run takes the single-pass form, one pass and one grid barrier per level
+        const bool ordered = shard_count > 1 || !count_ctr;
         CK(W.front[0].ensure((size_t)cap_ints * 4), "alloc frontier");
         CK(W.front[1].ensure((size_t)cap_ints * 4), "alloc frontier");
         CK(cudaMemcpyAsync(W.front[0].p, roots.data(), (size_t)F0 * sizeof(roots[0]), cudaMemcpyHostToDevice, st),
@@ -1129,7 +1206,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         long long *res = wtot + wcap + 1;
         int *sstat = reinterpret_cast<int *>(res + 4);
         constexpr long long SPLIT_MASKS = 1ll << 24;   // 64 MiB of replayed candidate ballots
-        const bool have_masks = W.smask.ensure((size_t)SPLIT_MASKS * 4) == cudaSuccess;
+        const bool have_masks = ordered && W.smask.ensure((size_t)SPLIT_MASKS * 4) == cudaSuccess;
         if (!have_masks) (void)cudaGetLastError();   // without the buffer the write pass tests again
         if (!W.ev2) {
             CK(cudaEventCreate(&W.ev2), "event");
@@ -1140,7 +1217,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                                                  W.front[1].as<int32_t>(), cap_ints, target, max_levels, wtot,
                                                  wcap, bar, res, sstat, count_ctr, directed ? 1 : 0,
                                                  serving ? 1 : 0, have_masks ? W.smask.as<uint32_t>() : nullptr,
-                                                 SPLIT_MASKS, st);
+                                                 SPLIT_MASKS, ordered ? 1 : 0, st);
         if (le == cudaSuccess) {
             ++launches;
             CK(cudaEventRecord(W.ev3, st), "event record");
@@ -1185,7 +1262,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             CK(cudaMemcpyAsync(&total, W.total.p, 8, cudaMemcpyDeviceToHost, st), "read split total");
             CK(cudaStreamSynchronize(st), "split sync");
             const long long need = total * (FRAME_HDR + depth + 1);
-            if (need > FRONTIER_MAX_INTS) break;   // keep the current frontier
+            if (need > front_ints) break;   // keep the current frontier
             CK(W.front[cur ^ 1].ensure((size_t)std::max<long long>(need, 1) * 4), "alloc frontier");
             CK(launch_split(W.jobs.as<JobDesc>(), W.front[cur].as<int32_t>(), F, depth, W.counts.as<int32_t>(),
                             W.offs.as<long long>(), W.front[cur ^ 1].as<int32_t>(), 1, count_ctr, directed ? 1 : 0,
@@ -1443,6 +1520,7 @@ sge_status prepare_pairs(sge_ctx *ctx, std::vector<PairReq> &reqs, const sge_opt
     if (o.kernel < 0 || o.kernel > 2) return fail(ctx, SGE_ERR_ARG, "unknown kernel family");
     if (o.domain_fixpoint < SGE_DOMAIN_AUTO || o.domain_fixpoint > SGE_DOMAIN_BLOCKS)
         return fail(ctx, SGE_ERR_ARG, "unknown domain fixpoint mode");
+    if (o.frontier_kib < 0) return fail(ctx, SGE_ERR_ARG, "negative frontier size");
     if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count))
         return fail(ctx, SGE_ERR_ARG, "shard index out of range");
     und.clear();
@@ -1882,6 +1960,7 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
             for (int v = 0; v < n; ++v)
                 lidx[(size_t)v] = (int32_t)(std::lower_bound(labs.begin(), labs.end(), vlabel[v]) - labs.begin());
             T->nlab = (int)L;
+            T->labs_h = labs;
             T->ltab_off = (int)((L + 3) & ~3LL);
             CK(T->ltab.ensure(((size_t)T->ltab_off + (size_t)n * L) * 4), "alloc label table");
             CK(cudaMemcpyAsync(T->ltab.p, labs.data(), (size_t)L * 4, cudaMemcpyHostToDevice, st), "upload labels");
@@ -1890,6 +1969,32 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
             CK(launch_label_nbmax(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), T->vld.as<int2>(),
                                   I.fill_out.as<int32_t>(), n, (int)L, T->ltab.as<int32_t>() + T->ltab_off, st),
                "label table");
+            if (n > BITSET_MAX_N) {
+                // label buckets: vertices by label index, descending degree within a label, so that
+                // a pattern vertex's initial domain is one bucket prefix (domain initialisation then
+                // touches its candidates only, not all n vertices)
+                std::vector<int2> vld_h((size_t)n);
+                CK(cudaMemcpyAsync(vld_h.data(), T->vld.p, (size_t)n * sizeof(int2), cudaMemcpyDeviceToHost, st),
+                   "read vertex records");
+                CK(cudaStreamSynchronize(st), "read vertex records");
+                std::vector<int32_t> ord((size_t)n);
+                for (int v = 0; v < n; ++v) ord[(size_t)v] = v;
+                std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+                    if (lidx[(size_t)a] != lidx[(size_t)b]) return lidx[(size_t)a] < lidx[(size_t)b];
+                    if (vld_h[(size_t)a].y != vld_h[(size_t)b].y) return vld_h[(size_t)a].y > vld_h[(size_t)b].y;
+                    return a < b;
+                });
+                std::vector<int32_t> bk((size_t)n * 2 + (size_t)L + 1);
+                for (int x = 0; x < n; ++x) {
+                    bk[(size_t)x] = ord[(size_t)x];
+                    bk[(size_t)n + x] = vld_h[(size_t)ord[(size_t)x]].y;
+                }
+                int32_t *start = bk.data() + 2 * (size_t)n;
+                for (long long l = 0; l <= L; ++l) start[l] = 0;
+                for (int v = 0; v < n; ++v) ++start[lidx[(size_t)v] + 1];
+                for (long long l = 0; l < L; ++l) start[l + 1] += start[l];
+                CK(upload(T->lbk, bk, st), "upload label buckets");
+            }
         }
     }
     if (!directed && n > 0 && n <= BITSET_MAX_N) {

@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(IB) k_ing_bits(const int32_t *rowptr, const in
         }
 }
 
-// Largest neighbour degree per (vertex, label): one warp per vertex, lanes over its row.
+// Largest neighbour degree per (label, vertex), label-major so that a warp reading consecutive
+// vertices of one label reads consecutive words: one warp per vertex, lanes over its row.
 __global__ void __launch_bounds__(IB) k_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld,
                                                     const int32_t *lidx, int n, int nlab, int32_t *nbmax) {
     const int lane = threadIdx.x & 31;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(IB) k_label_nbmax(const int32_t *rowptr, const
     for (long long v = w0; v < n; v += nw)
         for (int e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
             const int y = col[e];
-            atomicMax(nbmax + (size_t)v * nlab + lidx[y], vld[y].y);
+            atomicMax(nbmax + (size_t)lidx[y] * n + v, vld[y].y);
         }
 }
 

@@ -77,13 +77,19 @@ struct TargetView {
     const uint64_t *adj;        // adjacency bitset rows (undirected, small n) or null
     const int32_t *hub_slot;    // large undirected targets: bitset row of vertex v, or -1
     const uint64_t *hub_bits;   // hub rows, dw words each
-    // undirected targets: the distinct vertex labels (ascending, nlab of them) and, per vertex t
-    // and label index l, the largest degree among t's neighbours of that label (0: none), in
-    // nbmax[t * nlab + l]; null when not built (directed targets, or n x nlab above 2^26)
+    // undirected targets: the distinct vertex labels (ascending, nlab of them) and, per label
+    // index l and vertex t, the largest degree among t's neighbours of that label (0: none), in
+    // nbmax[l * n + t]; null when not built (directed targets, or n x nlab above 2^26)
     const int32_t *labs;
     const int32_t *nbmax;
     int32_t nlab;
     int32_t pad;
+    // large undirected targets: vertices grouped by label index (bucket l = [lbstart[l],
+    // lbstart[l + 1])), descending degree within a bucket, with those degrees in lbdeg; null
+    // otherwise.  A pattern vertex's initial domain is a prefix of its label's bucket.
+    const int32_t *lbuck;
+    const int32_t *lbdeg;
+    const int32_t *lbstart;
 };
 
 struct PatternView {
@@ -107,6 +113,8 @@ struct JobDesc {
     const BackEdge *back;
     uint64_t *filt;             // k x t.dw words: D(v) / label-degree filter, or null
     const int32_t *ulist;       // candidate lists of unparented RI-DS positions
+    const int32_t *plidx;       // RI-DS on a target with nbmax: each pattern vertex's label index among
+                                // the target's labels (-1: absent), else null
     int32_t k;
     int32_t flags;
     unsigned long long *ctr;    // [4]: matches, states, nodes, hash
@@ -173,6 +181,13 @@ inline void bind_control(SearchCtl &C, void *block) {
 // ------------------------------------------------------------ launchers
 // (implemented in sge_kernels.cu; all launch on `st`)
 
+// plidx of every job that has one: its pattern vertices' label indices (thread per vertex).
+cudaError_t launch_label_index(const JobDesc *jobs, const long long *vert_off, int njobs, long long nverts,
+                               cudaStream_t st);
+// Initial domains of the jobs whose targets have label buckets (their filter words already
+// zeroed): one warp per (job, pattern vertex), setting the bits of the bucket prefix.
+cudaError_t launch_domain_init_buckets(const JobDesc *jobs, const long long *vert_off, int njobs, long long nverts,
+                                       cudaStream_t st);
 cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
                                long long nunits, cudaStream_t st);
 cudaError_t launch_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff, int nent,
@@ -183,8 +198,11 @@ cudaError_t launch_domain_ac(const JobDesc *jobs, const int4 *ent, const long lo
 cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, const long long *sizes, int njobs,
                              int *changed, unsigned char *vchanged, cudaStream_t st);
 // Arc consistency and forward checking to their joint fixpoint, one block per
-// job (for batches of many jobs; no host round trips).
-cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, cudaStream_t st);
+// job (for batches of many jobs; no host round trips).  With `cand` null the
+// sweeps scan domain words; else they walk each vertex's candidate list
+// (slots [cstart[g], cstart[g] + csize[g]), g = vert_off[job] + v).
+cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, const long long *vert_off, const long long *cstart,
+                                   const long long *csize, int32_t *cand, cudaStream_t st);
 cudaError_t launch_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
                                 long long nverts, long long *sizes, cudaStream_t st);
 cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert,
@@ -203,7 +221,8 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
-                              int blocks_per_sm, uint32_t *masks, long long mask_total, cudaStream_t st);
+                              int blocks_per_sm, uint32_t *masks, long long mask_total, int ordered,
+                              cudaStream_t st);
 cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,
                         void *tmp, size_t tmp_bytes, cudaStream_t st);
 size_t scan_tmp_bytes(long long n);
@@ -246,7 +265,7 @@ cudaError_t launch_ingest_compact(const long long *off, const long long *uoff, c
 cudaError_t launch_ingest_degree(const int32_t *rowptr, int n, int32_t *deg, cudaStream_t st);
 cudaError_t launch_ingest_bits(const int32_t *rowptr, const int32_t *col, int n, int dw, uint64_t *bits,
                                cudaStream_t st);
-// nbmax[t * nlab + lidx[y]] = max deg(y) over the neighbours y of t (nbmax zeroed first).
+// nbmax[lidx[y] * n + t] = max deg(y) over the neighbours y of t (nbmax zeroed first).
 cudaError_t launch_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld, const int32_t *lidx, int n,
                                int nlab, int32_t *nbmax, cudaStream_t st);
 

@@ -191,51 +191,111 @@ __device__ __forceinline__ void emit_match(const JobDesc &J, const int *M, int l
 // ================================================================ domains
 
 // D(v) initialisation (Section 4): equal label, in/out-degree at least v's.
-// For RI it is exactly the rule 2-3 filter.  One warp per 64-bit word.
-__global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
-                                                       long long nunits) {
-    const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (u >= nunits) return;
-    const int j = find_job(unit_off, njobs, u);
+// For RI it is exactly the rule 2-3 filter.  One warp per 32 consecutive 64-bit words.
+// Each pattern vertex's label index among its job's target labels (-1: absent),
+// for the jobs that read the label-degree table; one thread per (job, vertex).
+__global__ void __launch_bounds__(BLOCK) k_label_index(const JobDesc *jobs, const long long *vert_off, int njobs,
+                                                       long long nverts) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nverts) return;
+    const int j = find_job(vert_off, njobs, g);
     const JobDesc &J = jobs[j];
-    if (J.filt == nullptr) return;
-    const bool DIR = (J.flags & JOB_DIRECTED) != 0;
-    const long long local = u - unit_off[j];
-    const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
-    const int lab = J.p.lab[v], od = J.p.odeg[v], id = DIR ? J.p.ideg[v] : 0;
-    // RI-DS on an undirected target without edge labels: a candidate t also needs, for every
-    // pattern neighbour u of v, a neighbour of its own with u's label and at least u's degree.
-    // That is arc consistency's test against the domains as initialised, so dropping the
-    // failures here removes only candidates the first sweep would remove; their rows, which
-    // the sweep would scan to the end, are never read.
-    const bool nbcheck = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && !DIR && J.t.nbmax != nullptr;
-    unsigned long long word = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int t = q * 64 + h * 32 + lane;
-        bool ok = false;
-        if (t < J.t.n) {
-            const int2 x = __ldg(J.t.vld + t);
-            ok = x.x == lab && x.y >= od && (!DIR || __ldg(J.t.indeg + t) >= id);
-        }
-        if (nbcheck && __any_sync(FULL, ok)) {
-            const int32_t *row = J.t.nbmax + (size_t)t * J.t.nlab;
-            for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) {
-                const int u = J.p.col[e];
-                const int lu = J.p.lab[u];
-                int lo = 0, hi = J.t.nlab;   // label index of lab(u) among the target's labels
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__ldg(J.t.labs + mid) < lu) lo = mid + 1; else hi = mid;
-                }
-                const bool has = lo < J.t.nlab && __ldg(J.t.labs + lo) == lu;
-                if (ok) ok = has && __ldg(row + lo) >= J.p.odeg[u];
+    if (J.plidx == nullptr) return;
+    const int u = (int)(g - vert_off[j]);
+    const int lab = J.p.lab[u];
+    int lo = 0, hi = J.t.nlab;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(J.t.labs + mid) < lab) lo = mid + 1; else hi = mid;
+    }
+    const_cast<int32_t *>(J.plidx)[u] = lo < J.t.nlab && __ldg(J.t.labs + lo) == lab ? lo : -1;
+}
+
+// Initial domain of pattern vertex v on a target with label buckets: the prefix of
+// lab(v)'s bucket with degree at least v's (descending order), then, for RI-DS, the
+// label-degree support test of k_domain_init; bits set with atomicOr into the zeroed filter.
+__global__ void __launch_bounds__(BLOCK) k_domain_init_buckets(const JobDesc *jobs, const long long *vert_off,
+                                                               int njobs, long long nverts) {
+    const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= nverts) return;
+    const int j = find_job(vert_off, njobs, g);
+    const JobDesc &J = jobs[j];
+    if (J.filt == nullptr || J.t.lbuck == nullptr) return;
+    const int v = (int)(g - vert_off[j]);
+    const int lab = J.p.lab[v], od = J.p.odeg[v];
+    int lo = 0, hi = J.t.nlab;   // lab(v)'s bucket
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(J.t.labs + mid) < lab) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= J.t.nlab || __ldg(J.t.labs + lo) != lab) return;   // label absent: empty domain
+    const int b0 = __ldg(J.t.lbstart + lo), b1 = __ldg(J.t.lbstart + lo + 1);
+    int e = b0, f = b1;          // first bucket position with degree below od (degrees descend)
+    while (e < f) {
+        const int mid = (e + f) >> 1;
+        if (__ldg(J.t.lbdeg + mid) >= od) e = mid + 1; else f = mid;
+    }
+    const bool nbcheck = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && J.t.nbmax != nullptr && J.plidx != nullptr;
+    uint64_t *Fv = J.filt + (size_t)v * J.t.dw;
+    for (int x = b0 + lane; x < e; x += 32) {
+        const int t = __ldg(J.t.lbuck + x);
+        bool ok = true;
+        if (nbcheck) {
+            for (int pe = J.p.rowptr[v]; pe < J.p.rowptr[v + 1] && ok; ++pe) {
+                const int pu = J.p.col[pe];
+                const int li = J.plidx[pu];
+                ok = li >= 0 && __ldg(J.t.nbmax + (size_t)li * J.t.n + t) >= J.p.odeg[pu];
             }
         }
-        word |= (unsigned long long)__ballot_sync(FULL, ok) << (32 * h);
+        if (ok) atomicOr((unsigned long long *)(Fv + (t >> 6)), 1ull << (t & 63));
     }
-    if (lane == 0) J.filt[(size_t)v * J.t.dw + q] = word;
+}
+
+constexpr int INIT_WORDS_PER_WARP = 32;   // consecutive filter words one warp of k_domain_init writes
+
+__global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
+                                                       long long nunits) {
+    const long long u0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * INIT_WORDS_PER_WARP;
+    const int lane = threadIdx.x & 31;
+    if (u0 >= nunits) return;
+    // the warp's words are consecutive units: find the job once, then step over its boundaries
+    int j = find_job(unit_off, njobs, u0);
+    for (long long u = u0; u < u0 + INIT_WORDS_PER_WARP && u < nunits; ++u) {
+        while (j + 1 < njobs && unit_off[j + 1] <= u) ++j;
+        const JobDesc &J = jobs[j];
+        if (J.filt == nullptr || J.t.lbuck != nullptr) continue;   // (bucket targets: k_domain_init_buckets)
+        const bool DIR = (J.flags & JOB_DIRECTED) != 0;
+        const long long local = u - unit_off[j];
+        const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
+        const int lab = J.p.lab[v], od = J.p.odeg[v], id = DIR ? J.p.ideg[v] : 0;
+        // RI-DS on an undirected target without edge labels: a candidate t also needs, for every
+        // pattern neighbour u of v, a neighbour of its own with u's label and at least u's degree.
+        // That is arc consistency's test against the domains as initialised, so dropping the
+        // failures here removes only candidates the first sweep would remove; their rows, which
+        // the sweep would scan to the end, are never read.
+        const bool nbcheck = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && !DIR && J.t.nbmax != nullptr &&
+                             J.plidx != nullptr;
+        unsigned long long word = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = q * 64 + h * 32 + lane;
+            bool ok = false;
+            if (t < J.t.n) {
+                const int2 x = __ldg(J.t.vld + t);
+                ok = x.x == lab && x.y >= od && (!DIR || __ldg(J.t.indeg + t) >= id);
+            }
+            if (nbcheck && __any_sync(FULL, ok)) {
+                for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) {
+                    const int pu = J.p.col[e];
+                    const int li = J.plidx[pu];   // lab(pu)'s index among the target's labels, -1 if absent
+                    if (ok) ok = li >= 0 && __ldg(J.t.nbmax + (size_t)li * J.t.n + t) >= J.p.odeg[pu];
+                }
+            }
+            word |= (unsigned long long)__ballot_sync(FULL, ok) << (32 * h);
+        }
+        if (lane == 0) J.filt[(size_t)v * J.t.dw + q] = word;
+    }
 }
 
 // Arc consistency of one candidate (Section 4): does target vertex t keep,
@@ -494,9 +554,21 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const 
 // Removals are monotone deletions, so this schedule reaches the same unique
 // greatest fixpoint as any other.  A forward-checking round that finds an
 // empty domain ends the job (it has no match).  Blocks stride over the jobs.
-__global__ void __launch_bounds__(BLOCK) k_domain_fixpoint(const JobDesc *jobs, int njobs) {
+// A sweep visits a dirty vertex's candidates either word by word (small
+// targets: `cand` null) or through its candidate list (large targets, whose
+// domain words are mostly empty: slots [cstart[g], cstart[g] + csize[g]) of
+// `cand`, g = vert_off[job] + v, a removed candidate's slot set to -1), 32
+// slots per warp step so that a candidate with a long row is checked by the
+// whole warp.
+constexpr int FIXPOINT_BIG_BLOCK = 1024;   // threads per block of k_domain_fixpoint when pairs are few
+
+__global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const JobDesc *jobs, int njobs,
+                                                                        const long long *vert_off,
+                                                           const long long *cstart, const long long *csize,
+                                                           int32_t *cand) {
     __shared__ unsigned char dirty[KMAX], chg[KMAX], done[KMAX];
     __shared__ int dl[KMAX], size[KMAX], elem[KMAX], newu[KMAX];
+    __shared__ long long pre[KMAX + 1];
     __shared__ int nd, any, nnew, empty;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
@@ -520,20 +592,74 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fixpoint(const JobDesc *jobs, 
                 __syncthreads();
                 const int n_d = nd;
                 if (n_d == 0) break;
-                const long long units = (long long)n_d * dw;
-                for (long long x = tid; x < units; x += blockDim.x) {
-                    const int i = (int)(x / dw), q = (int)(x - (long long)i * dw), v = dl[i];
-                    uint64_t *wp = J.filt + (size_t)v * dw + q;
-                    const uint64_t w0 = *wp;
-                    uint64_t keep = w0;
-                    for (uint64_t w = w0; w; w &= w - 1) {
-                        const int b = __ffsll((long long)w) - 1;
-                        if (!ac_supported(J, v, q * 64 + b, DIR, chk)) keep &= ~(1ull << b);
+                if (cand == nullptr) {
+                    const long long units = (long long)n_d * dw;
+                    for (long long x = tid; x < units; x += blockDim.x) {
+                        const int i = (int)(x / dw), q = (int)(x - (long long)i * dw), v = dl[i];
+                        uint64_t *wp = J.filt + (size_t)v * dw + q;
+                        const uint64_t w0 = *wp;
+                        uint64_t keep = w0;
+                        for (uint64_t w = w0; w; w &= w - 1) {
+                            const int b = __ffsll((long long)w) - 1;
+                            if (!ac_supported(J, v, q * 64 + b, DIR, chk)) keep &= ~(1ull << b);
+                        }
+                        if (keep != w0) {
+                            atomicAnd((unsigned long long *)wp, keep);
+                            chg[v] = 1;
+                            any = 1;
+                        }
                     }
-                    if (keep != w0) {
-                        atomicAnd((unsigned long long *)wp, keep);
-                        chg[v] = 1;
-                        any = 1;
+                } else {
+                    const long long g0 = vert_off[jb];
+                    if (tid == 0) {
+                        long long acc = 0;
+                        for (int i = 0; i < n_d; ++i) {
+                            pre[i] = acc;
+                            acc += csize[g0 + dl[i]];
+                        }
+                        pre[n_d] = acc;
+                    }
+                    __syncthreads();
+                    const long long units = pre[n_d];
+                    for (long long x0 = (long long)wid * 32; x0 < units; x0 += (long long)nwarps * 32) {
+                        const long long x = x0 + lane;
+                        int v = 0, t = -1;
+                        int32_t *slot = nullptr;
+                        if (x < units) {
+                            int lo = 0, hi = n_d;   // the dirty vertex whose slots hold unit x
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (pre[mid] <= x) lo = mid; else hi = mid;
+                            }
+                            v = dl[lo];
+                            slot = cand + cstart[g0 + v] + (x - pre[lo]);
+                            t = *slot;
+                        }
+                        bool drop = false, heavy = false;
+                        if (t >= 0) {
+                            if (!((J.filt[(size_t)v * dw + (t >> 6)] >> (t & 63)) & 1ull)) {
+                                *slot = -1;                      // removed by forward checking
+                            } else {
+                                const int len = __ldg(J.t.rowptr + t + 1) - __ldg(J.t.rowptr + t) +
+                                                (DIR ? __ldg(J.t.irowptr + t + 1) - __ldg(J.t.irowptr + t) : 0);
+                                heavy = len > AC_WARP_ROW;
+                                drop = !heavy && !ac_supported(J, v, t, DIR, chk);
+                            }
+                        }
+                        unsigned hv = __ballot_sync(FULL, heavy);
+                        while (hv) {
+                            const int L = __ffs(hv) - 1;
+                            hv &= hv - 1;
+                            const int vl = __shfl_sync(FULL, v, L), tl = __shfl_sync(FULL, t, L);
+                            const bool sup = ac_supported_warp(J, vl, tl, DIR, chk);
+                            if (lane == L) drop = !sup;
+                        }
+                        if (drop) {
+                            atomicAnd((unsigned long long *)(J.filt + (size_t)v * dw + (t >> 6)), ~(1ull << (t & 63)));
+                            *slot = -1;
+                            chg[v] = 1;
+                            any = 1;
+                        }
                     }
                 }
                 __syncthreads();
@@ -753,12 +879,16 @@ __global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int3
 
 // ========================================================= device split
 //
-// The breadth-first split as one cooperative launch: every level is a count
-// pass and a write pass over the current frontier, separated by a grid
-// barrier; children are appended atomically (their order is irrelevant
-// outside sharded runs).  The loop stops when the frontier reaches `target`
-// frames, is empty, would overflow `cap`, or `max_levels` levels are done.
-// Frames have a fixed stride (FRAME_HDR + kmax).
+// The breadth-first split as one cooperative launch.  Two forms:
+//  * ordered (k_split_coop): every level is a count pass, a scan of the
+//    warps' child counts and a write pass, so the children of a level come out
+//    in search order -- the order that frame i -> shard i mod S relies on;
+//  * single-pass (k_split_once, unsharded runs): every frame is tested once
+//    and each 32-candidate chunk appends its children at an offset reserved
+//    with one fetch-and-add, so a level costs one pass and one grid barrier.
+// The loop stops when the frontier reaches `target` frames, is empty, would
+// overflow `cap`, or `max_levels` levels are done.  All frames of a level
+// share its depth, so a level-L frame has stride FRAME_HDR + L.
 
 __device__ __forceinline__ long long block_excl_scan(long long x, long long *total);
 
@@ -945,6 +1075,125 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
                                         mcap, mp);
         grid_barrier(S.bar, S.bar + 1, S.status);
         F = total;
+        cur ^= 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.result[0] = F;
+        S.result[1] = cur;
+        S.result[2] = level;
+    }
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(S.result + 7), globaltimer());
+}
+
+// One frame of a single-pass split level: test its candidates once, add its
+// counters, and append the children of each chunk at offsets reserved on the
+// level's child counter `lvl_ctr`.  A reservation that ends past `cap_frames`
+// raises `full` and writes nothing (the level is then abandoned, see below).
+template <bool DIR>
+__device__ __forceinline__ void split_frame_once(const JobDesc *jobs, const int32_t *fr, int *M, int32_t *fout,
+                                                 int stride, long long cap_frames,
+                                                 unsigned long long *lvl_ctr, long long *full) {
+    const int lane = threadIdx.x & 31;
+    const int j = fr[0], depth = fr[1], rbeg = fr[2], rend = fr[3];
+    const JobDesc &J = jobs[j];
+    const bool leaf = depth + 1 == J.k;
+    for (int t = lane; t < depth; t += 32) M[t] = fr[FRAME_HDR + t];
+    __syncwarp();
+    const PosInfo P = J.pos[depth];
+    const Src src = cand_source(J, P, M);
+    const int c_lo = rbeg >= 0 ? rbeg : 0, c_hi = rbeg >= 0 ? min(rend, src.len) : src.len;
+    unsigned long long psum = 0, nodes = 0, hs = 0;
+    if (leaf) {
+        for (int t = lane; t < depth; t += 32) psum += gterm(J.pos[t].pv, M[t]);
+        psum = warp_sum(psum);
+    }
+    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+        const int idx = c0 + lane;
+        bool ok = false;
+        int c = -1;
+        if (idx < c_hi) {
+            c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
+            ok = feasible<DIR>(J, P, depth, c, (src.ptr && P.par >= 0) ? src.base + idx : -1, M);
+        }
+        const unsigned bal = __ballot_sync(FULL, ok);
+        const int cnt = __popc(bal);
+        nodes += cnt;
+        if (leaf) {
+            if (ok) {
+                hs += fmix64(psum + gterm(P.pv, c));
+                if (J.mbuf) emit_match(J, M, depth, c);
+            }
+        } else if (cnt > 0) {
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(lvl_ctr, (unsigned long long)cnt);
+            at = __shfl_sync(FULL, at, 0);
+            if ((long long)(at + cnt) <= cap_frames) {
+                if (ok) {
+                    int32_t *dst = fout + (long long)(at + __popc(bal & ((1u << lane) - 1u))) * stride;
+                    dst[0] = j; dst[1] = depth + 1; dst[2] = -1; dst[3] = -1;
+                    for (int t = 0; t < depth; ++t) dst[FRAME_HDR + t] = M[t];
+                    dst[FRAME_HDR + depth] = c;
+                }
+            } else if (lane == 0) {
+                *(volatile long long *)full = 1;
+            }
+        }
+    }
+    hs = warp_sum(hs);
+    if (lane == 0) {
+        if (rbeg <= 0) atomicAdd(J.ctr + 1, (unsigned long long)src.len);
+        atomicAdd(J.ctr + 2, nodes);
+        if (leaf) {
+            atomicAdd(J.ctr + 0, nodes);
+            atomicAdd(J.ctr + 3, hs);
+        }
+    }
+    __syncwarp();
+}
+
+// Single-pass split (unsharded runs; the caller's shard counts the levels).
+// The children of level L are counted on wtot[L] (zeroed by the host).  A
+// level whose children do not all fit is abandoned after its barrier: its
+// frames stay the frontier, rewritten so that the search does not count the
+// level again -- a frame with children becomes a counted range over its whole
+// candidate list (the search re-derives its children and counts from the next
+// level on), a frame on the last position becomes the empty range [1, 1).
+template <bool DIR>
+__global__ void __launch_bounds__(BLOCK) k_split_once(const JobDesc *jobs, long long f0, SplitCtl S) {
+    __shared__ int Msh[WARPS_PER_BLOCK][KMAX];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *M = Msh[wib];
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    unsigned long long *lvl_ctr = reinterpret_cast<unsigned long long *>(S.wtot);
+    long long F = f0;
+    int cur = 0, level = 0;
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(S.result + 6), ~globaltimer());
+    for (; level < S.max_levels; ++level) {
+        if (F == 0 || F >= S.target) break;
+        int32_t *fin = cur ? S.buf1 : S.buf0;
+        int32_t *fout = cur ? S.buf0 : S.buf1;
+        const int sin = FRAME_HDR + level, sout = FRAME_HDR + level + 1;
+        const long long lo = F * w / nw, hi = F * (w + 1) / nw;
+        for (long long f = lo; f < hi; ++f)
+            split_frame_once<DIR>(jobs, fin + f * sin, M, fout, sout, S.cap_ints / sout, lvl_ctr + level,
+                                  S.result + 5);
+        grid_barrier(S.bar, S.bar + 1, S.status);
+        if (*(volatile long long *)(S.result + 5) != 0) {
+            for (long long f = lo; f < hi; ++f) {
+                int32_t *fr = fin + f * sin;
+                if (lane == 0) {
+                    const bool leaf = fr[1] + 1 == jobs[fr[0]].k;
+                    if (leaf) { fr[2] = 1; fr[3] = 1; }
+                    else {
+                        fr[1] |= FRAME_COUNTED;
+                        if (fr[2] < 0) { fr[2] = 0; fr[3] = 0x7fffffff; }
+                    }
+                }
+            }
+            break;
+        }
+        F = (long long)*(volatile unsigned long long *)(lvl_ctr + level);
         cur ^= 1;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1647,7 +1896,11 @@ constexpr uint8_t LIST_SPILLED = 0xff;
 
 // Pattern-size class of a bitset-kernel launch: its per-warp shared layout is
 // fixed at compile time for patterns of at most KM vertices.
-__host__ __device__ constexpr int bits_km(int kmax) { return kmax <= 32 ? 32 : (kmax <= 64 ? 64 : KMAX); }
+// (A smaller class keeps shared memory, and so the L1 left beside it for the adjacency rows,
+// no larger than the patterns need: 24 vertices take 31 KB per block, 32 take 42 KB.)
+__host__ __device__ constexpr int bits_km(int kmax) {
+    return kmax <= 24 ? 24 : (kmax <= 32 ? 32 : (kmax <= 64 ? 64 : KMAX));
+}
 
 struct __align__(16) PosB {
     int16_t pv, par, bb, bc;  // pattern vertex, parent position, back edges [bb, bb + bc) other than
@@ -1665,7 +1918,7 @@ constexpr int32_t ABYTES_MASK = (1 << 28) - 1;
 // the survivor lists and their lengths, and the back-edge positions.
 template <int KM>
 struct BitsLayout {
-    static constexpr int LCAP = KM <= 32 ? 64 : 16;
+    static constexpr int LCAP = KM <= 32 ? 64 : 16;   // (KM 24 and 32: 64 entries)
     static constexpr size_t TAB = 0;
     static constexpr size_t FRANGE = TAB + (size_t)KM * 16;
     static constexpr size_t MOFF = FRANGE + 8;
@@ -1676,8 +1929,12 @@ struct BitsLayout {
 };
 
 __host__ __device__ __forceinline__ size_t bits_smem_per_warp(int kmax, int nwl) {
-    return bits_km(kmax) == 32 ? BitsLayout<32>::BYTES
-                               : (bits_km(kmax) == 64 ? BitsLayout<64>::BYTES : BitsLayout<KMAX>::BYTES);
+    switch (bits_km(kmax)) {
+        case 24: return BitsLayout<24>::BYTES;
+        case 32: return BitsLayout<32>::BYTES;
+        case 64: return BitsLayout<64>::BYTES;
+        default: return BitsLayout<KMAX>::BYTES;
+    }
 }
 
 __host__ __device__ __forceinline__ size_t bits_slab_words_per_warp(int kmax, int nwl) {
@@ -1704,11 +1961,11 @@ struct BitsWarp {
     // warp sync; larger ones keep them in shared memory.
     int lcr;
     __device__ __forceinline__ int lc(int l) const {
-        if constexpr (KM == 32) return __shfl_sync(FULL, lcr, l);
+        if constexpr (KM <= 32) return __shfl_sync(FULL, lcr, l);
         else return lcnt()[l];
     }
     __device__ __forceinline__ void set_lc(int l, int v) {
-        if constexpr (KM == 32) {
+        if constexpr (KM <= 32) {
             lcr = (threadIdx.x & 31) == l ? v : lcr;
         } else {
             __syncwarp();
@@ -2189,10 +2446,25 @@ unsigned grid_for(long long warps) {
 
 // ================================================================ launchers
 
+cudaError_t launch_domain_init_buckets(const JobDesc *jobs, const long long *vert_off, int njobs, long long nverts,
+                                       cudaStream_t st) {
+    if (nverts <= 0) return cudaSuccess;
+    k_domain_init_buckets<<<grid_for(nverts), BLOCK, 0, st>>>(jobs, vert_off, njobs, nverts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_label_index(const JobDesc *jobs, const long long *vert_off, int njobs, long long nverts,
+                               cudaStream_t st) {
+    if (nverts <= 0) return cudaSuccess;
+    k_label_index<<<(unsigned)((nverts + BLOCK - 1) / BLOCK), BLOCK, 0, st>>>(jobs, vert_off, njobs, nverts);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs, long long nunits,
                                cudaStream_t st) {
     if (nunits <= 0) return cudaSuccess;
-    k_domain_init<<<grid_for(nunits), BLOCK, 0, st>>>(jobs, unit_off, njobs, nunits);
+    k_domain_init<<<grid_for((nunits + INIT_WORDS_PER_WARP - 1) / INIT_WORDS_PER_WARP), BLOCK, 0, st>>>(
+        jobs, unit_off, njobs, nunits);
     return cudaGetLastError();
 }
 
@@ -2219,14 +2491,17 @@ cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, cudaStream_t st) {
+cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, const long long *vert_off, const long long *cstart,
+                                   const long long *csize, int32_t *cand, cudaStream_t st) {
     if (njobs <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    // few pairs: one large block each, so that they still fill the device
+    const int threads = njobs < sms * 4 ? FIXPOINT_BIG_BLOCK : BLOCK;
     const int grid = njobs < sms * 8 ? njobs : sms * 8;
-    k_domain_fixpoint<<<grid, BLOCK, 0, st>>>(jobs, njobs);
+    k_domain_fixpoint<<<grid, threads, 0, st>>>(jobs, njobs, vert_off, cstart, csize, cand);
     return cudaGetLastError();
 }
 
@@ -2260,7 +2535,8 @@ cudaError_t launch_split(const JobDesc *jobs, const int32_t *fin, long long nf, 
 cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, int32_t *buf1, long long cap_ints,
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
-                              int blocks_per_sm, uint32_t *masks, long long mask_total, cudaStream_t st) {
+                              int blocks_per_sm, uint32_t *masks, long long mask_total, int ordered,
+                              cudaStream_t st) {
     SplitCtl S;
     S.buf0 = buf0; S.buf1 = buf1; S.cap_ints = cap_ints; S.target = target; S.max_levels = max_levels;
     S.wtot = wtot; S.bar = bar; S.result = result; S.status = status; S.count_ctr = count_ctr;
@@ -2270,7 +2546,8 @@ cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, 
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    void *fn = directed ? (void *)k_split_coop<true> : (void *)k_split_coop<false>;
+    void *fn = ordered ? (directed ? (void *)k_split_coop<true> : (void *)k_split_coop<false>)
+                       : (directed ? (void *)k_split_once<true> : (void *)k_split_once<false>);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BLOCK, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -2374,15 +2651,18 @@ cudaError_t search_blocks_per_sm(int kernel, int kmax, int nwl, int directed, in
     if (kernel == 2) {
         switch (nwl) {
             case 1:
-                return kmax <= 32 ? occupancy_of(k_search_bits<1, 32>, smem, occ)
+                return kmax <= 24 ? occupancy_of(k_search_bits<1, 24>, smem, occ)
+                       : kmax <= 32 ? occupancy_of(k_search_bits<1, 32>, smem, occ)
                        : kmax <= 64 ? occupancy_of(k_search_bits<1, 64>, smem, occ)
                                     : occupancy_of(k_search_bits<1, KMAX>, smem, occ);
             case 2:
-                return kmax <= 32 ? occupancy_of(k_search_bits<2, 32>, smem, occ)
+                return kmax <= 24 ? occupancy_of(k_search_bits<2, 24>, smem, occ)
+                       : kmax <= 32 ? occupancy_of(k_search_bits<2, 32>, smem, occ)
                        : kmax <= 64 ? occupancy_of(k_search_bits<2, 64>, smem, occ)
                                     : occupancy_of(k_search_bits<2, KMAX>, smem, occ);
             case 4:
-                return kmax <= 32 ? occupancy_of(k_search_bits<4, 32>, smem, occ)
+                return kmax <= 24 ? occupancy_of(k_search_bits<4, 24>, smem, occ)
+                       : kmax <= 32 ? occupancy_of(k_search_bits<4, 32>, smem, occ)
                        : kmax <= 64 ? occupancy_of(k_search_bits<4, 64>, smem, occ)
                                     : occupancy_of(k_search_bits<4, KMAX>, smem, occ);
             default: return cudaErrorInvalidValue;
@@ -2420,21 +2700,27 @@ cudaError_t launch_search(int kernel, const JobDesc *jobs, const SearchCtl &ctl,
     if (kernel == 2) {
         switch (nwl) {
             case 1:
-                return kmax <= 32 ? launch_persistent(k_search_bits<1, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
+                return kmax <= 24 ? launch_persistent(k_search_bits<1, 24>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                      max_grid, grid_out, st)
+                       : kmax <= 32 ? launch_persistent(k_search_bits<1, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                       max_grid, grid_out, st)
                        : kmax <= 64 ? launch_persistent(k_search_bits<1, 64>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                         max_grid, grid_out, st)
                                     : launch_persistent(k_search_bits<1, KMAX>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                         max_grid, grid_out, st);
             case 2:
-                return kmax <= 32 ? launch_persistent(k_search_bits<2, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
+                return kmax <= 24 ? launch_persistent(k_search_bits<2, 24>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                      max_grid, grid_out, st)
+                       : kmax <= 32 ? launch_persistent(k_search_bits<2, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                       max_grid, grid_out, st)
                        : kmax <= 64 ? launch_persistent(k_search_bits<2, 64>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                         max_grid, grid_out, st)
                                     : launch_persistent(k_search_bits<2, KMAX>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                         max_grid, grid_out, st);
             case 4:
-                return kmax <= 32 ? launch_persistent(k_search_bits<4, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
+                return kmax <= 24 ? launch_persistent(k_search_bits<4, 24>, jobs, ctl, kmax, smem, blocks_per_sm,
+                                                      max_grid, grid_out, st)
+                       : kmax <= 32 ? launch_persistent(k_search_bits<4, 32>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                       max_grid, grid_out, st)
                        : kmax <= 64 ? launch_persistent(k_search_bits<4, 64>, jobs, ctl, kmax, smem, blocks_per_sm,
                                                         max_grid, grid_out, st)
