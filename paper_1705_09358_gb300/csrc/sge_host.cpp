@@ -279,6 +279,7 @@ struct TargetRec {
     DevBuf rowptr, col, elab, irowptr, icol, ielab, vld, indeg, adj, hub_slot, hub_bits, hub_list;
     DevBuf ltab;           // distinct labels, then the per-(label, vertex) largest neighbour degree
     int nlab = 0, ltab_off = 0;
+    int maxdeg = 0;                // longest out- or in-row
     std::vector<int32_t> labs_h;   // host copy of the distinct labels (ascending)
     DevBuf lbk;            // large targets: label buckets (vertices, their degrees, bucket starts)
     TargetView view() const {
@@ -300,7 +301,7 @@ struct TargetRec {
         v.labs = ltab.p ? ltab.as<int32_t>() : nullptr;
         v.nbmax = ltab.p ? ltab.as<int32_t>() + ltab_off : nullptr;
         v.nlab = ltab.p ? nlab : 0;
-        v.pad = 0;
+        v.maxdeg = maxdeg;
         v.lbuck = lbk.p ? lbk.as<int32_t>() : nullptr;
         v.lbdeg = lbk.p ? lbk.as<int32_t>() + n : nullptr;
         v.lbstart = lbk.p ? lbk.as<int32_t>() + 2 * (size_t)n : nullptr;
@@ -376,6 +377,9 @@ struct Workspace {
     DevBuf pool, pseq, ctl, slab;
     DevBuf mbuf, ckpt, wtrace, smask, plidx, cstart;
     std::vector<JobDesc> hdesc;   // host job records, reused
+    std::vector<JobDesc> hfdesc;  // host records of the jobs with a filter block, reused
+    std::vector<long long> hsizes;  // host copy of the domain sizes, reused
+    std::vector<unsigned long long> hctr;  // host copy of the job counters, reused
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;   // search kernel, split kernel
     cudaStream_t bound = nullptr;
 #define SGE_WS_BUFFERS                                                                                             \
@@ -630,7 +634,7 @@ struct Job {
     long long filt_off = -1;  // offset (u64 words) of the job's filter block
     long long vert_off = 0;   // offset in the sizes array
     std::vector<int> mu, par;
-    std::vector<long long> dsize;
+    const long long *dsize = nullptr;   // |D(v)| of the job's pattern vertices (RI-DS), in the workspace
 };
 
 struct PairReq {
@@ -806,8 +810,9 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             }
         }
     }
-    std::vector<JobDesc> fdesc;
     bool any_buckets = false;
+    unit_off.reserve(fjobs.size());
+    vert_off.reserve(fjobs.size());
     for (int q : fjobs) {
         unit_off.push_back(nunits);
         vert_off.push_back(nverts);
@@ -816,11 +821,19 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         if (!jobs[q].t->lbk.p) nunits += (long long)jobs[q].p->k * jobs[q].t->dw;
         else any_buckets = true;
         nverts += jobs[q].p->k;
-        fdesc.push_back(desc[q]);
     }
     const int nf = (int)fjobs.size();
     if (nf > 0) {
-        CK(upload(W.fjobs, fdesc, st), "upload domain jobs");
+        if (nf == nj) {
+            CK(upload(W.fjobs, desc, st), "upload domain jobs");   // every job has a filter block
+        } else {
+            std::vector<JobDesc> &fdesc = W.hfdesc;
+            fdesc.resize((size_t)nf);
+            parallel_for(nf, [&](int x0, int x1) {
+                for (int x = x0; x < x1; ++x) fdesc[(size_t)x] = desc[(size_t)fjobs[x]];
+            });
+            CK(upload(W.fjobs, fdesc, st), "upload domain jobs");
+        }
         CK(upload(W.unit_off, unit_off, st), "upload unit offsets");
         CK(upload(W.vert_off, vert_off, st), "upload vertex offsets");
         if (any_plidx) {
@@ -859,7 +872,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                                     (o.domain_fixpoint == SGE_DOMAIN_BLOCKS ||
                                      (o.domain_fixpoint == SGE_DOMAIN_AUTO && nrids >= ctx->sms / 2));
         if (block_fixpoint) {
-            CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, nullptr, nullptr, nullptr, nullptr, st),
+            CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, nullptr, nullptr, nullptr, nullptr,
+                                      W.flag.as<int>() + 8, st),
                "domain fixpoint");
             ++launches;
             if (trace_on()) {
@@ -935,7 +949,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                 CK(upload(W.cstart, cs, st), "upload candidate list offsets");
                 CK(launch_domain_fixpoint(W.fjobs.as<JobDesc>(), nf, W.vert_off.as<long long>(),
                                           W.cstart.as<long long>(), W.cstart.as<long long>() + nverts,
-                                          W.cand.as<int32_t>(), st), "domain fixpoint");
+                                          W.cand.as<int32_t>(), W.flag.as<int>() + 8, st), "domain fixpoint");
                 ++launches;
                 if (trace_on()) {
                     CK(cudaStreamSynchronize(st), "fixpoint sync");
@@ -1019,16 +1033,19 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         CK(launch_domain_sizes(W.fjobs.as<JobDesc>(), W.vert_off.as<long long>(), nf, nverts,
                                W.sizes.as<long long>(), st), "domain sizes");
         ++launches;
-        std::vector<long long> sizes((size_t)nverts);
+        std::vector<long long> &sizes = W.hsizes;   // kept across calls (no fresh pages)
+        if (sizes.size() < (size_t)nverts) sizes.resize((size_t)nverts);
         CK(cudaMemcpyAsync(sizes.data(), W.sizes.p, (size_t)nverts * 8, cudaMemcpyDeviceToHost, st), "read sizes");
         CK(cudaStreamSynchronize(st), "sizes sync");
-        for (int q : fjobs) {
-            Job &J = jobs[q];
-            J.dsize.assign(sizes.begin() + J.vert_off, sizes.begin() + J.vert_off + J.p->k);
-            if (J.algo != SGE_RI)
-                for (long long s : J.dsize)
-                    if (s == 0) J.active = false;   // an empty domain: no match, no search
-        }
+        parallel_for(nf, [&](int x0, int x1) {
+            for (int x = x0; x < x1; ++x) {
+                Job &J = jobs[fjobs[x]];
+                J.dsize = sizes.data() + J.vert_off;
+                if (J.algo != SGE_RI)
+                    for (int v = 0; v < J.p->k; ++v)
+                        if (J.dsize[v] == 0) J.active = false;   // an empty domain: no match, no search
+            }
+        });
     }
     trace_phase(st, "domains", t_start);
     // orderings and position tables; RI tables depend only on the pattern and
@@ -1053,8 +1070,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         for (int q = q0; q < q1; ++q) {
             Job &J = jobs[q];
             if (!J.active || J.algo == SGE_RI) continue;
-            gcf_order(*J.p, J.algo, J.dsize.data(), J.mu, J.par);
-            build_positions(*J.p, J.mu, J.par, J.algo, J.dsize.data(), J.t->n, jpos[(size_t)q], jback[(size_t)q]);
+            gcf_order(*J.p, J.algo, J.dsize, J.mu, J.par);
+            build_positions(*J.p, J.mu, J.par, J.algo, J.dsize, J.t->n, jpos[(size_t)q], jback[(size_t)q]);
         }
     }, 64);
     for (int q = 0; q < nj; ++q) {
@@ -1121,6 +1138,15 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             JobDesc &D = desc[q];
             D.pos = W.pos.as<PosInfo>() + pos_off[q];
             D.back = W.back.as<BackEdge>() + back_off[q];
+            if (jobs[q].active) {
+                // can a position after the first have more than SPLIT_RANGE candidates?
+                bool longl = jobs[q].t->maxdeg == 0 || jobs[q].t->maxdeg > SPLIT_RANGE;
+                for (int i = 1; i < D.k && !longl; ++i) {
+                    const PosInfo &P = pos[(size_t)pos_off[q] + i];
+                    longl = P.par < 0 && ((D.flags & JOB_RIDS) ? (long long)P.ucnt : jobs[q].t->n) > SPLIT_RANGE;
+                }
+                if (longl) D.flags |= JOB_LONG_LISTS;
+            }
             D.ulist = W.ulist.as<int32_t>();
             if (enumerate) {
                 D.mbuf = W.mbuf.as<int32_t>();
@@ -1198,7 +1224,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         CK(cudaMemcpyAsync(W.front[0].p, roots.data(), (size_t)F0 * sizeof(roots[0]), cudaMemcpyHostToDevice, st),
            "upload roots");
         const long long wcap = (long long)ctx->sms * 32 * search_warps_per_block();
-        const size_t ctl_words = (size_t)wcap + 16;
+        const size_t ctl_words = (size_t)wcap + 16 + 2 * KMAX;   // (+ the level trace)
         CK(W.splitctl.ensure(ctl_words * 8), "alloc split control");
         CK(cudaMemsetAsync(W.splitctl.p, 0, ctl_words * 8, st), "clear split control");
         long long *wtot = W.splitctl.as<long long>();
@@ -1217,7 +1243,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                                                  W.front[1].as<int32_t>(), cap_ints, target, max_levels, wtot,
                                                  wcap, bar, res, sstat, count_ctr, directed ? 1 : 0,
                                                  serving ? 1 : 0, have_masks ? W.smask.as<uint32_t>() : nullptr,
-                                                 SPLIT_MASKS, ordered ? 1 : 0, st);
+                                                 SPLIT_MASKS, ordered ? 1 : 0,
+                                                 trace_on() ? wtot + wcap + 16 : nullptr, st);
         if (le == cudaSuccess) {
             ++launches;
             CK(cudaEventRecord(W.ev3, st), "event record");
@@ -1234,9 +1261,22 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             depth = (int)r4[2];
             fstride = FRAME_HDR + depth;
             split_done = true;
-            if (trace_on())
+            if (trace_on()) {
                 std::fprintf(stderr, "[sge] device split: %d levels, %lld frames at %.3f ms\n", depth, F,
                              now_ms() - t_start);
+                if (!ordered) {
+                    // per level: end time, children, longest candidate list of one frame
+                    std::vector<long long> tr((size_t)2 * KMAX), lv((size_t)std::max(depth, 1));
+                    CK(cudaMemcpy(tr.data(), wtot + wcap + 16, tr.size() * 8, cudaMemcpyDeviceToHost), "read trace");
+                    CK(cudaMemcpy(lv.data(), wtot, lv.size() * 8, cudaMemcpyDeviceToHost), "read trace");
+                    long long prev = ~r4[6];
+                    for (int l = 0; l < depth; ++l) {
+                        std::fprintf(stderr, "[sge]   level %d: %.1f us, %lld children, longest list %lld\n", l,
+                                     (tr[(size_t)l] - prev) * 1e-3, lv[(size_t)l], tr[(size_t)KMAX + l]);
+                        prev = tr[(size_t)l];
+                    }
+                }
+            }
         } else {
             (void)cudaGetLastError();   // cooperative launch refused: split level by level below
         }
@@ -1464,31 +1504,34 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             if (ckpt_kmax) *ckpt_kmax = kmax;
         }
     }
-    std::vector<unsigned long long> ctr((size_t)nj * 6);
+    std::vector<unsigned long long> &ctr = W.hctr;   // kept across calls (no fresh pages)
+    if (ctr.size() < (size_t)nj * 6) ctr.resize((size_t)nj * 6);
     CK(cudaMemcpyAsync(ctr.data(), W.ctr.p, (size_t)nj * 6 * 8, cudaMemcpyDeviceToHost, st), "read counters");
     CK(cudaStreamSynchronize(st), "counter sync");
     const double t_end = now_ms();
-    for (int q = 0; q < nj; ++q) {
-        sge_result &r = out[jobs[q].pair];
-        std::memset(&r, 0, sizeof(r));
-        r.matches = ctr[4 * (size_t)q + 0];
-        r.states = ctr[4 * (size_t)q + 1];
-        r.nodes = ctr[4 * (size_t)q + 2];
-        r.hash = ctr[4 * (size_t)q + 3];
-        r.preprocess_ms = t_pre - t_start;
-        r.match_ms = t_end - t_pre;
-        r.search_kernel_ms = kernel_ms;
-        r.split_kernel_ms = split_ms;
-        r.split_exec_ms = split_exec_ms;
-        r.search_exec_ms = search_exec_ms;
-        r.frames = F;
-        r.donations = donations;
-        r.alg_bytes = kernel == SGE_KERNEL_BITSET ? ctr[5 * (size_t)nj + q] : 12ull * r.states;
-        r.launches = launches;
-        r.split_depth = depth;
-        r.status = status;
-        r.kernel = kernel;
-    }
+    parallel_for(nj, [&](int q0, int q1) {
+        for (int q = q0; q < q1; ++q) {
+            sge_result &r = out[jobs[q].pair];
+            std::memset(&r, 0, sizeof(r));
+            r.matches = ctr[4 * (size_t)q + 0];
+            r.states = ctr[4 * (size_t)q + 1];
+            r.nodes = ctr[4 * (size_t)q + 2];
+            r.hash = ctr[4 * (size_t)q + 3];
+            r.preprocess_ms = t_pre - t_start;
+            r.match_ms = t_end - t_pre;
+            r.search_kernel_ms = kernel_ms;
+            r.split_kernel_ms = split_ms;
+            r.split_exec_ms = split_exec_ms;
+            r.search_exec_ms = search_exec_ms;
+            r.frames = F;
+            r.donations = donations;
+            r.alg_bytes = kernel == SGE_KERNEL_BITSET ? ctr[5 * (size_t)nj + q] : 12ull * r.states;
+            r.launches = launches;
+            r.split_depth = depth;
+            r.status = status;
+            r.kernel = kernel;
+        }
+    });
     if (enumerate && match_rows && nj == 1) {
         const long long produced = (long long)ctr[4 * (size_t)nj + 0];
         const long long rows = std::min(produced, match_cap);
@@ -1948,6 +1991,9 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
     }
     CK(T->vld.ensure(nv * sizeof(int2)), "alloc vertex info");
     CK(launch_make_vld(T->rowptr.as<int32_t>(), I.vlab.as<int32_t>(), T->vld.as<int2>(), n, st), "vertex info");
+    int32_t *d_maxdeg = I.small.as<int32_t>() + 3;   // (zeroed with the ingest flags)
+    CK(launch_ingest_maxdeg(T->rowptr.as<int32_t>(), n, d_maxdeg, st), "longest row");
+    if (directed) CK(launch_ingest_maxdeg(T->irowptr.as<int32_t>(), n, d_maxdeg, st), "longest row");
     if (!directed && n > 0) {
         // the largest neighbour degree per (vertex, label): domain initialisation reads it to
         // drop, at once, the candidates that have no neighbour able to carry some pattern edge
@@ -2003,9 +2049,11 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
         CK(launch_ingest_bits(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), n, T->dw, T->adj.as<uint64_t>(), st),
            "adjacency bitset");
     }
-    int hflags = 0;
-    CK(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st), "read ingest flags");
+    int32_t hsmall[4] = {0, 0, 0, 0};   // flags, long out-rows, long in-rows, longest row
+    CK(cudaMemcpyAsync(hsmall, flags, sizeof(hsmall), cudaMemcpyDeviceToHost, st), "read ingest flags");
     CK(cudaStreamSynchronize(st), "target ingest");
+    const int hflags = hsmall[0];
+    T->maxdeg = hsmall[3];
     const char *bad = (hflags & ING_RANGE) ? "edge endpoint out of range"
                       : (hflags & ING_LOOP) ? "self-loop"
                       : (hflags & ING_LABEL) ? "repeated edge with a different label" : nullptr;

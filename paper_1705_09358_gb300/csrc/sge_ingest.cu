@@ -196,6 +196,16 @@ __global__ void __launch_bounds__(IB) k_ing_degree(const int32_t *rowptr, int n,
         deg[v] = rowptr[v + 1] - rowptr[v];
 }
 
+// The longest row, folded into *maxdeg with one atomicMax per warp.
+__global__ void __launch_bounds__(IB) k_ing_maxdeg(const int32_t *rowptr, int n, int32_t *maxdeg) {
+    int m = 0;
+    for (long long v = blockIdx.x * (long long)IB + threadIdx.x; v < n; v += (long long)gridDim.x * IB)
+        m = max(m, rowptr[v + 1] - rowptr[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(maxdeg, m);
+}
+
 // Adjacency bitset rows (undirected, n <= the bitset limit): one warp per row.
 __global__ void __launch_bounds__(IB) k_ing_bits(const int32_t *rowptr, const int32_t *col, int n, int dw,
                                                  uint64_t *bits) {
@@ -271,6 +281,12 @@ cudaError_t launch_ingest_compact(const long long *off, const long long *uoff, c
 cudaError_t launch_ingest_degree(const int32_t *rowptr, int n, int32_t *deg, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_ing_degree<<<blocks_for(n, IB), IB, 0, st>>>(rowptr, n, deg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_maxdeg(const int32_t *rowptr, int n, int32_t *maxdeg, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_ing_maxdeg<<<blocks_for(n, IB), IB, 0, st>>>(rowptr, n, maxdeg);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,11 @@ constexpr int JOB_RIDS = 1;          // test v_t in D(mu_i) for every candidate
 constexpr int JOB_ELAB = 2;          // compare edge labels
 constexpr int JOB_DIRECTED = 4;
 constexpr int JOB_FC = 8;            // forward checking of singleton domains
+constexpr int JOB_LONG_LISTS = 16;   // some position after the first may have more than SPLIT_RANGE candidates
+
+// The breadth-first split writes a child whose candidate list is longer than
+// this as range frames of this many candidates each.
+constexpr int SPLIT_RANGE = 256;
 
 // One search position i of a job: pattern vertex mu_i and its constraints.
 struct PosInfo {
@@ -83,7 +88,7 @@ struct TargetView {
     const int32_t *labs;
     const int32_t *nbmax;
     int32_t nlab;
-    int32_t pad;
+    int32_t maxdeg;             // longest out- or in-row (0: not known)
     // large undirected targets: vertices grouped by label index (bucket l = [lbstart[l],
     // lbstart[l + 1])), descending degree within a bucket, with those degrees in lbdeg; null
     // otherwise.  A pattern vertex's initial domain is a prefix of its label's bucket.
@@ -200,9 +205,10 @@ cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, con
 // Arc consistency and forward checking to their joint fixpoint, one block per
 // job (for batches of many jobs; no host round trips).  With `cand` null the
 // sweeps scan domain words; else they walk each vertex's candidate list
-// (slots [cstart[g], cstart[g] + csize[g]), g = vert_off[job] + v).
+// (slots [cstart[g], cstart[g] + csize[g]), g = vert_off[job] + v).  Blocks
+// take jobs from the counter `next_job` (one int of device scratch, zeroed here).
 cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, const long long *vert_off, const long long *cstart,
-                                   const long long *csize, int32_t *cand, cudaStream_t st);
+                                   const long long *csize, int32_t *cand, int *next_job, cudaStream_t st);
 cudaError_t launch_domain_sizes(const JobDesc *jobs, const long long *vert_off, int njobs,
                                 long long nverts, long long *sizes, cudaStream_t st);
 cudaError_t launch_domain_lists(const JobDesc *jobs, const int *task_job, const int *task_vert,
@@ -222,7 +228,7 @@ cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, 
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
                               int blocks_per_sm, uint32_t *masks, long long mask_total, int ordered,
-                              cudaStream_t st);
+                              long long *trace, cudaStream_t st);
 cudaError_t launch_scan(const int32_t *in, long long *out, long long n, long long *total,
                         void *tmp, size_t tmp_bytes, cudaStream_t st);
 size_t scan_tmp_bytes(long long n);
@@ -263,6 +269,7 @@ cudaError_t launch_ingest_compact(const long long *off, const long long *uoff, c
                                   const long long *utotal, const uint64_t *keys, int n, int32_t *rowptr, int32_t *col,
                                   int32_t *lab, cudaStream_t st);
 cudaError_t launch_ingest_degree(const int32_t *rowptr, int n, int32_t *deg, cudaStream_t st);
+cudaError_t launch_ingest_maxdeg(const int32_t *rowptr, int n, int32_t *maxdeg, cudaStream_t st);
 cudaError_t launch_ingest_bits(const int32_t *rowptr, const int32_t *col, int n, int dw, uint64_t *bits,
                                cudaStream_t st);
 // nbmax[lidx[y] * n + t] = max deg(y) over the neighbours y of t (nbmax zeroed first).

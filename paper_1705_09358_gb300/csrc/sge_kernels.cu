@@ -24,6 +24,8 @@
 
 #include <cuda/atomic>
 
+#include <algorithm>
+
 namespace sge {
 
 namespace {
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const 
 // from the other domains, and the loop goes on until neither changes anything.
 // Removals are monotone deletions, so this schedule reaches the same unique
 // greatest fixpoint as any other.  A forward-checking round that finds an
-// empty domain ends the job (it has no match).  Blocks stride over the jobs.
+// empty domain ends the job (it has no match).  Blocks take jobs from a counter.
 // A sweep visits a dirty vertex's candidates either word by word (small
 // targets: `cand` null) or through its candidate list (large targets, whose
 // domain words are mostly empty: slots [cstart[g], cstart[g] + csize[g]) of
@@ -561,17 +563,69 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const 
 // slots per warp step so that a candidate with a long row is checked by the
 // whole warp.
 constexpr int FIXPOINT_BIG_BLOCK = 1024;   // threads per block of k_domain_fixpoint when pairs are few
+constexpr int FP_CHUNK = 1024;             // domain words scanned at once by k_domain_fixpoint
 
-__global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const JobDesc *jobs, int njobs,
+// Exclusive scan of one int per thread over the block (up to 1024 threads);
+// `total` receives the block's sum.  wsum: 32 ints of shared memory.
+__device__ __forceinline__ int block_scan_int(int x, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) wsum[lane] = s;
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    const int before = wid ? wsum[wid - 1] : 0;
+    __syncthreads();   // wsum may be reused at once
+    return before + incl - x;
+}
+
+// Position of the r-th (0-based) set bit of w (r < popcount(w)).
+__device__ __forceinline__ int select_bit(uint64_t w, int r) {
+    int base = 0;
+    uint32_t h = (uint32_t)w;
+    const int pl = __popc(h);
+    if (r >= pl) {
+        r -= pl;
+        h = (uint32_t)(w >> 32);
+        base = 32;
+    }
+    for (int i = 0; i < r; ++i) h &= h - 1;
+    return base + __ffs(h) - 1;
+}
+
+__global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const JobDesc *jobs, int njobs,
                                                                         const long long *vert_off,
                                                            const long long *cstart, const long long *csize,
-                                                           int32_t *cand) {
+                                                           int32_t *cand, int *next_job) {
     __shared__ unsigned char dirty[KMAX], chg[KMAX], done[KMAX];
     __shared__ int dl[KMAX], size[KMAX], elem[KMAX], newu[KMAX];
     __shared__ long long pre[KMAX + 1];
     __shared__ int nd, any, nnew, empty;
+    __shared__ uint64_t wsnap[FP_CHUNK];
+    __shared__ int wpre[FP_CHUNK + 1], wsum[32];
+    __shared__ int jnext;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
-    for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    for (;;) {
+        // the next job, taken dynamically: pairs differ widely in cost
+        if (tid == 0) jnext = atomicAdd(next_job, 1);
+        __syncthreads();
+        const int jb = jnext;
+        __syncthreads();
+        if (jb >= njobs) break;
         const JobDesc &J = jobs[jb];
         if (J.filt == nullptr || !(J.flags & JOB_RIDS)) continue;
         const bool DIR = (J.flags & JOB_DIRECTED) != 0, chk = (J.flags & JOB_ELAB) != 0;
@@ -580,7 +634,19 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const Jo
         for (int v = tid; v < k; v += blockDim.x) { dirty[v] = 1; done[v] = 0; }
         if (tid == 0) empty = 0;
         __syncthreads();
-        for (;;) {
+        // |D(v)|, kept exact below: every removal counts it down, and the first domain to
+        // empty ends the pair (it has no match, so the rest of its fixpoint is never needed)
+        for (int v = wid; v < k; v += nwarps) {
+            unsigned long long c = 0;
+            for (int q = lane; q < dw; q += 32) c += __popcll(J.filt[(size_t)v * dw + q]);
+            c = warp_sum(c);
+            if (lane == 0) {
+                size[v] = (int)c;
+                if (c == 0) empty = 1;
+            }
+        }
+        __syncthreads();
+        while (!empty) {
             // ---- arc consistency over the dirty vertices, to its fixpoint
             for (;;) {
                 if (tid == 0) { nd = 0; any = 0; }
@@ -593,21 +659,51 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const Jo
                 const int n_d = nd;
                 if (n_d == 0) break;
                 if (cand == nullptr) {
+                    // the dirty domains' words, FP_CHUNK at a time: snapshot them, scan their
+                    // popcounts, and give each thread the next set bit, so the candidates of a
+                    // dense word are checked in parallel rather than by one thread in turn
                     const long long units = (long long)n_d * dw;
-                    for (long long x = tid; x < units; x += blockDim.x) {
-                        const int i = (int)(x / dw), q = (int)(x - (long long)i * dw), v = dl[i];
-                        uint64_t *wp = J.filt + (size_t)v * dw + q;
-                        const uint64_t w0 = *wp;
-                        uint64_t keep = w0;
-                        for (uint64_t w = w0; w; w &= w - 1) {
-                            const int b = __ffsll((long long)w) - 1;
-                            if (!ac_supported(J, v, q * 64 + b, DIR, chk)) keep &= ~(1ull << b);
+                    const int ipt = FP_CHUNK / blockDim.x;   // words per thread in the scan
+                    for (long long u0 = 0; u0 < units; u0 += FP_CHUNK) {
+                        const int nw_c = (int)min((long long)FP_CHUNK, units - u0);
+                        int cnt = 0;
+                        for (int r = 0; r < ipt; ++r) {
+                            const int iw = tid * ipt + r;
+                            uint64_t w = 0;
+                            if (iw < nw_c) {
+                                const long long x = u0 + iw;
+                                const int i = (int)(x / dw), q = (int)(x - (long long)i * dw);
+                                w = J.filt[(size_t)dl[i] * dw + q];
+                            }
+                            wsnap[iw] = w;
+                            cnt += __popcll(w);
                         }
-                        if (keep != w0) {
-                            atomicAnd((unsigned long long *)wp, keep);
-                            chg[v] = 1;
-                            any = 1;
+                        int total;
+                        int ex = block_scan_int(cnt, wsum, total);
+                        for (int r = 0; r < ipt; ++r) {
+                            const int iw = tid * ipt + r;
+                            wpre[iw] = ex;
+                            ex += __popcll(wsnap[iw]);
                         }
+                        if (tid == 0) wpre[FP_CHUNK] = total;
+                        __syncthreads();
+                        for (int x = tid; x < total; x += blockDim.x) {
+                            int lo = 0, hi = nw_c;   // the word holding set bit x: wpre[lo] <= x < wpre[lo + 1]
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (wpre[mid] <= x) lo = mid; else hi = mid;
+                            }
+                            const long long ux = u0 + lo;
+                            const int i = (int)(ux / dw), q = (int)(ux - (long long)i * dw), v = dl[i];
+                            const int b = select_bit(wsnap[lo], x - wpre[lo]);
+                            if (!ac_supported(J, v, q * 64 + b, DIR, chk)) {
+                                atomicAnd((unsigned long long *)(J.filt + (size_t)v * dw + q), ~(1ull << b));
+                                chg[v] = 1;
+                                any = 1;
+                                if (atomicSub(&size[v], 1) == 1) empty = 1;
+                            }
+                        }
+                        __syncthreads();   // wsnap and wpre are refilled for the next chunk
                     }
                 } else {
                     const long long g0 = vert_off[jb];
@@ -659,11 +755,12 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const Jo
                             *slot = -1;
                             chg[v] = 1;
                             any = 1;
+                            if (atomicSub(&size[v], 1) == 1) empty = 1;
                         }
                     }
                 }
                 __syncthreads();
-                if (!any) break;
+                if (empty || !any) break;
                 // the pattern neighbours of every shrunk domain are checked again
                 for (int v = tid; v < k; v += blockDim.x) {
                     if (!chg[v]) continue;
@@ -673,20 +770,10 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const Jo
                 }
                 __syncthreads();
             }
-            if (!FC) break;
-            // ---- one forward-checking round: |D(v)| by warps, then the new singletons
-            for (int v = wid; v < k; v += nwarps) {
-                unsigned long long c = 0;
-                for (int q = lane; q < dw; q += 32) c += __popcll(J.filt[(size_t)v * dw + q]);
-                c = warp_sum(c);
-                if (lane == 0) {
-                    size[v] = (int)c;
-                    if (c == 0) empty = 1;
-                }
-            }
+            if (empty || !FC) break;
+            // ---- one forward-checking round on the new singletons
             if (tid == 0) nnew = 0;
             __syncthreads();
-            if (empty) break;   // an empty domain: no match, nothing more to prune
             for (int v = tid; v < k; v += blockDim.x) {
                 chg[v] = 0;
                 if (size[v] == 1 && !done[v]) {
@@ -722,10 +809,11 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK) k_domain_fixpoint(const Jo
                 if (atomicAnd(wp, ~bit) & bit) {
                     chg[v] = 1;
                     any = 1;
+                    if (atomicSub(&size[v], 1) == 1) empty = 1;
                 }
             }
             __syncthreads();
-            if (!any) break;
+            if (empty || !any) break;
             for (int v = tid; v < k; v += blockDim.x) {
                 if (!chg[v]) continue;
                 for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) dirty[J.p.col[e]] = 1;
@@ -932,6 +1020,8 @@ struct SplitCtl {
     int count_ctr;              // 0 in shards other than 0: levels above the frontier are counted once
     uint32_t *masks;            // candidate ballots of the count pass, replayed by the write pass
     long long mask_total;       // masks in the buffer (each warp owns mask_total / warps of them)
+    long long *trace;           // single-pass split, tracing only (else null): [0, KMAX) each level's end
+                                // (device clock), [KMAX, 2 KMAX) its longest candidate list of one frame
 };
 
 // One frame of a split level: count its children (pass 0) or write them from
@@ -1085,14 +1175,37 @@ __global__ void __launch_bounds__(BLOCK) k_split_coop(const JobDesc *jobs, long 
     if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(S.result + 7), globaltimer());
 }
 
+// Counters of the single-pass split, summed per warp while consecutive frames
+// belong to one job and added to the job's counters on a job change or at the
+// end of the warp's slice (lane 0), so a level of many frames does not queue
+// thousands of atomics on one job's four words.
+struct SplitAcc {
+    int job;
+    unsigned long long st, nd, mt, hs;
+};
+
+// (lane 0 only; the warp's SplitAcc lives in shared memory)
+__device__ __forceinline__ void split_acc_flush(const JobDesc *jobs, SplitAcc &A) {
+    if (A.job >= 0) {
+        unsigned long long *ctr = jobs[A.job].ctr;
+        if (A.st) atomicAdd(ctr + 1, A.st);
+        if (A.nd) atomicAdd(ctr + 2, A.nd);
+        if (A.mt) atomicAdd(ctr + 0, A.mt);
+        if (A.hs) atomicAdd(ctr + 3, A.hs);
+    }
+    A.job = -1;
+    A.st = A.nd = A.mt = A.hs = 0;
+}
+
 // One frame of a single-pass split level: test its candidates once, add its
-// counters, and append the children of each chunk at offsets reserved on the
-// level's child counter `lvl_ctr`.  A reservation that ends past `cap_frames`
-// raises `full` and writes nothing (the level is then abandoned, see below).
+// counters to A, and append the children of each chunk at offsets reserved on
+// the level's child counter `lvl_ctr`.  A reservation that ends past
+// `cap_frames` raises `full` and writes nothing (the level is then abandoned,
+// see below).  Returns the frame's candidate range length.
 template <bool DIR>
-__device__ __forceinline__ void split_frame_once(const JobDesc *jobs, const int32_t *fr, int *M, int32_t *fout,
-                                                 int stride, long long cap_frames,
-                                                 unsigned long long *lvl_ctr, long long *full) {
+__device__ __forceinline__ int split_frame_once(const JobDesc *jobs, const int32_t *fr, int *M, int32_t *fout,
+                                                int stride, long long cap_frames, unsigned long long *lvl_ctr,
+                                                long long *full, SplitAcc &A) {
     const int lane = threadIdx.x & 31;
     const int j = fr[0], depth = fr[1], rbeg = fr[2], rend = fr[3];
     const JobDesc &J = jobs[j];
@@ -1106,6 +1219,22 @@ __device__ __forceinline__ void split_frame_once(const JobDesc *jobs, const int3
     if (leaf) {
         for (int t = lane; t < depth; t += 32) psum += gterm(J.pos[t].pv, M[t]);
         psum = warp_sum(psum);
+    }
+    // the children's position: where its candidates come from
+    // a child whose own candidate list is longer than SPLIT_RANGE is written as range
+    // frames, so that no warp of the next level scans a hub's whole row while the
+    // others wait at the level's barrier (JOB_LONG_LISTS: such a list can occur)
+    PosInfo Q;
+    const int32_t *qrow = nullptr;
+    bool ranges = false;
+    if (!leaf && (J.flags & JOB_LONG_LISTS)) {
+        Q = J.pos[depth + 1];
+        if (Q.par >= 0) {
+            qrow = (Q.flags & POS_IN_ROW) ? J.t.irowptr : J.t.rowptr;
+            ranges = J.t.maxdeg == 0 || J.t.maxdeg > SPLIT_RANGE;
+        } else {
+            ranges = ((J.flags & JOB_RIDS) ? Q.ucnt : J.t.n) > SPLIT_RANGE;
+        }
     }
     for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
         const int idx = c0 + lane;
@@ -1124,13 +1253,41 @@ __device__ __forceinline__ void split_frame_once(const JobDesc *jobs, const int3
                 if (J.mbuf) emit_match(J, M, depth, c);
             }
         } else if (cnt > 0) {
+            // frames per child: one, or one per SPLIT_RANGE candidates of a long list
+            int r = ok ? 1 : 0;
+            if (ok && ranges) {
+                int len;
+                if (qrow) {
+                    const int a = Q.par == depth ? c : M[Q.par];
+                    len = __ldg(qrow + a + 1) - __ldg(qrow + a);
+                } else {
+                    len = (J.flags & JOB_RIDS) ? Q.ucnt : J.t.n;
+                }
+                r = len > SPLIT_RANGE ? (len + SPLIT_RANGE - 1) / SPLIT_RANGE : 1;
+            }
+            int incl, total;
+            if (ranges) {
+                incl = r;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                total = __shfl_sync(FULL, incl, 31);
+            } else {
+                incl = __popc(bal & (0xffffffffu >> (31 - lane)));   // survivors up to this lane
+                total = cnt;
+            }
             unsigned long long at = 0;
-            if (lane == 0) at = atomicAdd(lvl_ctr, (unsigned long long)cnt);
+            if (lane == 0) at = atomicAdd(lvl_ctr, (unsigned long long)total);
             at = __shfl_sync(FULL, at, 0);
-            if ((long long)(at + cnt) <= cap_frames) {
-                if (ok) {
-                    int32_t *dst = fout + (long long)(at + __popc(bal & ((1u << lane) - 1u))) * stride;
-                    dst[0] = j; dst[1] = depth + 1; dst[2] = -1; dst[3] = -1;
+            if ((long long)(at + total) <= cap_frames) {
+                for (int q = 0; q < r; ++q) {
+                    int32_t *dst = fout + (long long)(at + incl - r + q) * stride;
+                    dst[0] = j;
+                    dst[1] = depth + 1;
+                    dst[2] = r == 1 ? -1 : q * SPLIT_RANGE;
+                    dst[3] = r == 1 ? -1 : (q + 1 == r ? 0x7fffffff : (q + 1) * SPLIT_RANGE);
                     for (int t = 0; t < depth; ++t) dst[FRAME_HDR + t] = M[t];
                     dst[FRAME_HDR + depth] = c;
                 }
@@ -1141,33 +1298,45 @@ __device__ __forceinline__ void split_frame_once(const JobDesc *jobs, const int3
     }
     hs = warp_sum(hs);
     if (lane == 0) {
-        if (rbeg <= 0) atomicAdd(J.ctr + 1, (unsigned long long)src.len);
-        atomicAdd(J.ctr + 2, nodes);
+        if (A.job != j) {
+            split_acc_flush(jobs, A);
+            A.job = j;
+        }
+        if (rbeg <= 0) A.st += (unsigned long long)src.len;
+        A.nd += nodes;
         if (leaf) {
-            atomicAdd(J.ctr + 0, nodes);
-            atomicAdd(J.ctr + 3, hs);
+            A.mt += nodes;
+            A.hs += hs;
         }
     }
     __syncwarp();
+    return c_hi - c_lo;
 }
 
 // Single-pass split (unsharded runs; the caller's shard counts the levels).
 // The children of level L are counted on wtot[L] (zeroed by the host).  A
 // level whose children do not all fit is abandoned after its barrier: its
 // frames stay the frontier, rewritten so that the search does not count the
-// level again -- a frame with children becomes a counted range over its whole
-// candidate list (the search re-derives its children and counts from the next
-// level on), a frame on the last position becomes the empty range [1, 1).
+// level again -- a frame with children becomes a counted range (over its
+// whole candidate list if it had none; the search re-derives its children
+// and counts from the next level on), a frame on the last position becomes
+// the empty range [1, 1).
 template <bool DIR>
-__global__ void __launch_bounds__(BLOCK) k_split_once(const JobDesc *jobs, long long f0, SplitCtl S) {
+__global__ void __launch_bounds__(BLOCK, 4) k_split_once(const JobDesc *jobs, long long f0, SplitCtl S) {
     __shared__ int Msh[WARPS_PER_BLOCK][KMAX];
+    __shared__ SplitAcc Ash[WARPS_PER_BLOCK];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *M = Msh[wib];
+    SplitAcc &A = Ash[wib];
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long *lvl_ctr = reinterpret_cast<unsigned long long *>(S.wtot);
     long long F = f0;
     int cur = 0, level = 0;
+    if (lane == 0) {
+        A.job = -1;
+        A.st = A.nd = A.mt = A.hs = 0;
+    }
     if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(S.result + 6), ~globaltimer());
     for (; level < S.max_levels; ++level) {
         if (F == 0 || F >= S.target) break;
@@ -1175,10 +1344,15 @@ __global__ void __launch_bounds__(BLOCK) k_split_once(const JobDesc *jobs, long 
         int32_t *fout = cur ? S.buf0 : S.buf1;
         const int sin = FRAME_HDR + level, sout = FRAME_HDR + level + 1;
         const long long lo = F * w / nw, hi = F * (w + 1) / nw;
+        int longest = 0;
         for (long long f = lo; f < hi; ++f)
-            split_frame_once<DIR>(jobs, fin + f * sin, M, fout, sout, S.cap_ints / sout, lvl_ctr + level,
-                                  S.result + 5);
+            longest = max(longest, split_frame_once<DIR>(jobs, fin + f * sin, M, fout, sout, S.cap_ints / sout,
+                                                         lvl_ctr + level, S.result + 5, A));
+        if (lane == 0) split_acc_flush(jobs, A);
+        if (S.trace && lane == 0 && longest > 0)
+            atomicMax(reinterpret_cast<unsigned long long *>(S.trace + KMAX + level), (unsigned long long)longest);
         grid_barrier(S.bar, S.bar + 1, S.status);
+        if (S.trace && blockIdx.x == 0 && threadIdx.x == 0) S.trace[level] = (long long)globaltimer();
         if (*(volatile long long *)(S.result + 5) != 0) {
             for (long long f = lo; f < hi; ++f) {
                 int32_t *fr = fin + f * sin;
@@ -2492,16 +2666,23 @@ cudaError_t launch_domain_fc(const JobDesc *jobs, const long long *vert_off, con
 }
 
 cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, const long long *vert_off, const long long *cstart,
-                                   const long long *csize, int32_t *cand, cudaStream_t st) {
+                                   const long long *csize, int32_t *cand, int *next_job, cudaStream_t st) {
     if (njobs <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // few pairs: one large block each, so that they still fill the device
+    // few pairs: one large block each, so that they still fill the device; many pairs:
+    // as many blocks as are resident at once, each taking pairs from the counter
     const int threads = njobs < sms * 4 ? FIXPOINT_BIG_BLOCK : BLOCK;
-    const int grid = njobs < sms * 8 ? njobs : sms * 8;
-    k_domain_fixpoint<<<grid, threads, 0, st>>>(jobs, njobs, vert_off, cstart, csize, cand);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_domain_fixpoint, threads, 0);
+    if (e != cudaSuccess) return e;
+    const long long wave = (long long)sms * std::max(occ, 1);
+    const int grid = (int)std::min<long long>(njobs, wave);
+    e = cudaMemsetAsync(next_job, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_domain_fixpoint<<<grid, threads, 0, st>>>(jobs, njobs, vert_off, cstart, csize, cand, next_job);
     return cudaGetLastError();
 }
 
@@ -2536,8 +2717,9 @@ cudaError_t launch_split_coop(const JobDesc *jobs, long long f0, int32_t *buf0, 
                               long long target, int max_levels, long long *wtot, long long wtot_cap,
                               unsigned *bar, long long *result, int *status, int count_ctr, int directed,
                               int blocks_per_sm, uint32_t *masks, long long mask_total, int ordered,
-                              cudaStream_t st) {
+                              long long *trace, cudaStream_t st) {
     SplitCtl S;
+    S.trace = ordered ? nullptr : trace;
     S.buf0 = buf0; S.buf1 = buf1; S.cap_ints = cap_ints; S.target = target; S.max_levels = max_levels;
     S.wtot = wtot; S.bar = bar; S.result = result; S.status = status; S.count_ctr = count_ctr;
     S.masks = masks; S.mask_total = masks ? mask_total : 0;
