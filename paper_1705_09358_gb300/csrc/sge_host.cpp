@@ -594,6 +594,8 @@ int build_positions_into(const PatView &P, const int *mu, const int *par, int al
         } else {
             p.ucnt = algo == SGE_RI ? n : (int)dsize[v];
         }
+        for (int j = 0; j < i; ++j)
+            if (P.lab[mu[j]] == p.lab) p.same[j >> 6] |= 1ull << (j & 63);
         p.bbeg = nb;
         for (int j = 0; j < i; ++j) {
             const int w = mu[j];

@@ -58,6 +58,8 @@ struct PosInfo {
     int32_t uoff;   // unparented RI-DS: offset of D(mu_i) in the job's candidate list
     int32_t flags;  // POS_IN_ROW
     int32_t pad;
+    uint64_t same[2];   // bit j (j < i): mu_j has lab(mu_i).  Only those positions can already hold a
+                        // candidate of mu_i (any other image has another label), so rule 1 checks them alone
 };
 
 // A pattern edge from mu_i back to an earlier position j (rule 4).

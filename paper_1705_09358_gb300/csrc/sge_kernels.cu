@@ -65,6 +65,12 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
     return x;
 }
 
+__device__ __forceinline__ int warp_max(int x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(FULL, x, o));
+    return x;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -167,8 +173,10 @@ __device__ __forceinline__ bool feasible(const JobDesc &J, const PosInfo &P, int
             if ((be.dir & 2) && !row_has(J.t.rowptr, J.t.col, J.t.elab, x, c, be.lab_in, chk)) return false;
         }
     }
-    for (int j = 0; j < i; ++j)                                           // rule 1
-        if (M[j] == c) return false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)                                           // rule 1 (same-label positions)
+        for (uint64_t m = P.same[h]; m; m &= m - 1)
+            if (M[64 * h + __ffsll((long long)m) - 1] == c) return false;
     return true;
 }
 
@@ -261,15 +269,28 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
     const long long u0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * INIT_WORDS_PER_WARP;
     const int lane = threadIdx.x & 31;
     if (u0 >= nunits) return;
-    // the warp's words are consecutive units: find the job once, then step over its boundaries
+    // the warp's words are consecutive units: find the job once, then step over its
+    // boundaries; (v, q) = (pattern vertex, word) steps along with u (a job holds
+    // k x dw < 2^15 units, so 32-bit arithmetic)
     int j = find_job(unit_off, njobs, u0);
+    int v = -1, q = 0;
     for (long long u = u0; u < u0 + INIT_WORDS_PER_WARP && u < nunits; ++u) {
-        while (j + 1 < njobs && unit_off[j + 1] <= u) ++j;
+        bool moved = false;
+        while (j + 1 < njobs && unit_off[j + 1] <= u) {
+            ++j;
+            moved = true;
+        }
         const JobDesc &J = jobs[j];
+        if (v < 0 || moved) {
+            const int local = (int)(u - unit_off[j]);
+            v = local / J.t.dw;
+            q = local - v * J.t.dw;
+        } else if (++q == J.t.dw) {
+            q = 0;
+            ++v;
+        }
         if (J.filt == nullptr || J.t.lbuck != nullptr) continue;   // (bucket targets: k_domain_init_buckets)
         const bool DIR = (J.flags & JOB_DIRECTED) != 0;
-        const long long local = u - unit_off[j];
-        const int v = (int)(local / J.t.dw), q = (int)(local % J.t.dw);
         const int lab = J.p.lab[v], od = J.p.odeg[v], id = DIR ? J.p.ideg[v] : 0;
         // RI-DS on an undirected target without edge labels: a candidate t also needs, for every
         // pattern neighbour u of v, a neighbour of its own with u's label and at least u's degree.
@@ -672,7 +693,7 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const
                             uint64_t w = 0;
                             if (iw < nw_c) {
                                 const long long x = u0 + iw;
-                                const int i = (int)(x / dw), q = (int)(x - (long long)i * dw);
+                                const int i = (int)x / dw, q = (int)x - i * dw;
                                 w = J.filt[(size_t)dl[i] * dw + q];
                             }
                             wsnap[iw] = w;
@@ -694,7 +715,7 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const
                                 if (wpre[mid] <= x) lo = mid; else hi = mid;
                             }
                             const long long ux = u0 + lo;
-                            const int i = (int)(ux / dw), q = (int)(ux - (long long)i * dw), v = dl[i];
+                            const int i = (int)ux / dw, q = (int)ux - i * dw, v = dl[i];
                             const int b = select_bit(wsnap[lo], x - wpre[lo]);
                             if (!ac_supported(J, v, q * 64 + b, DIR, chk)) {
                                 atomicAnd((unsigned long long *)(J.filt + (size_t)v * dw + q), ~(1ull << b));
@@ -1212,7 +1233,7 @@ __device__ __forceinline__ int split_frame_once(const JobDesc *jobs, const int32
     const bool leaf = depth + 1 == J.k;
     for (int t = lane; t < depth; t += 32) M[t] = fr[FRAME_HDR + t];
     __syncwarp();
-    const PosInfo P = J.pos[depth];
+    const PosInfo &P = J.pos[depth];
     const Src src = cand_source(J, P, M);
     const int c_lo = rbeg >= 0 ? rbeg : 0, c_hi = rbeg >= 0 ? min(rend, src.len) : src.len;
     unsigned long long psum = 0, nodes = 0, hs = 0;
@@ -1313,6 +1334,152 @@ __device__ __forceinline__ int split_frame_once(const JobDesc *jobs, const int32
     return c_hi - c_lo;
 }
 
+// A split frame with at most this many candidates is expanded by one lane.
+constexpr int SPLIT_LANE_MAX = 8;
+
+// Frames of candidates a child of position depth + 1 takes: one, or one per
+// SPLIT_RANGE candidates when its list is longer (JOB_LONG_LISTS pairs only).
+__device__ __forceinline__ int split_child_frames(const JobDesc &J, int depth, int c, const int *M) {
+    if (!(J.flags & JOB_LONG_LISTS)) return 1;
+    const PosInfo &Q = J.pos[depth + 1];
+    long long len;
+    if (Q.par >= 0) {
+        if (J.t.maxdeg != 0 && J.t.maxdeg <= SPLIT_RANGE) return 1;
+        const int32_t *rp = (Q.flags & POS_IN_ROW) ? J.t.irowptr : J.t.rowptr;
+        const int a = Q.par == depth ? c : M[Q.par];
+        len = __ldg(rp + a + 1) - __ldg(rp + a);
+    } else {
+        len = (J.flags & JOB_RIDS) ? Q.ucnt : J.t.n;
+    }
+    return len > SPLIT_RANGE ? (int)((len + SPLIT_RANGE - 1) / SPLIT_RANGE) : 1;
+}
+
+// The next 32 frames of a warp's slice [f0, hi) of a single-pass split level,
+// one per lane where a frame has at most 32 candidates: the lane tests them in
+// turn (a warp on such a frame would leave most lanes idle), reading the
+// frame's images straight from the frontier.  Children are appended at offsets
+// from one fetch-and-add per warp; counters are summed over runs of lanes with
+// the same job and added with one atomic per run.  Returns the lanes whose
+// frames have longer ranges (the caller expands them a warp at a time) and
+// raises `longest` to the longest range seen.
+template <bool DIR>
+__device__ unsigned split_lane_frames(const JobDesc *jobs, const int32_t *fin, long long f0, long long hi, int depth,
+                                      int32_t *fout, long long cap_frames, unsigned long long *lvl_ctr,
+                                      long long *full, int &longest) {
+    const int lane = threadIdx.x & 31;
+    const int sin = FRAME_HDR + depth, sout = sin + 1;
+    const long long f = f0 + lane;
+    const bool have = f < hi;
+    const int32_t *fr = fin + (have ? f : f0) * sin;
+    const int *Mg = fr + FRAME_HDR;
+    int j = 0, rbeg = -1, c_lo = 0, c_hi = 0;
+    Src src;
+    src.ptr = nullptr; src.base = 0; src.len = 0;
+    if (have) {
+        j = fr[0];
+        rbeg = fr[2];
+        const int rend = fr[3];
+        src = cand_source(jobs[j], jobs[j].pos[depth], Mg);
+        c_lo = rbeg >= 0 ? rbeg : 0;
+        c_hi = rbeg >= 0 ? min(rend, src.len) : src.len;
+        longest = max(longest, c_hi - c_lo);
+    }
+    const bool mine = have && c_hi - c_lo <= SPLIT_LANE_MAX;
+    const unsigned longm = __ballot_sync(FULL, have && !mine);
+    if (!__any_sync(FULL, mine)) return longm;
+    const JobDesc &J = jobs[j];
+    const PosInfo &P = J.pos[depth];   // (read where used: a copy would hold 16 registers)
+    const bool leaf = depth + 1 == J.k;
+    unsigned mask = 0;   // the lane's survivors, bit i for candidate c_lo + i
+    int nch = 0;         // frames its children take
+    unsigned long long st = 0, nd = 0, mt = 0, hs = 0;
+    if (mine) {
+        for (int i = 0; i < c_hi - c_lo; ++i) {
+            const int idx = c_lo + i;
+            const int c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
+            if (feasible<DIR>(J, P, depth, c, (src.ptr && P.par >= 0) ? src.base + idx : -1, Mg)) mask |= 1u << i;
+        }
+        nd = __popc(mask);
+        if (rbeg <= 0) st = (unsigned long long)src.len;
+        if (leaf) {
+            mt = nd;
+            if (mask) {
+                unsigned long long psum = 0;
+                for (int t = 0; t < depth; ++t) psum += gterm(J.pos[t].pv, Mg[t]);
+                for (unsigned m = mask; m; m &= m - 1) {
+                    const int idx = c_lo + __ffs(m) - 1;
+                    const int c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
+                    hs += fmix64(psum + gterm(P.pv, c));
+                    if (J.mbuf) emit_match(J, Mg, depth, c);
+                }
+            }
+        } else {
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int idx = c_lo + __ffs(m) - 1;
+                const int c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
+                nch += split_child_frames(J, depth, c, Mg);
+            }
+        }
+    }
+    // children: one reservation for the warp
+    int incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (total > 0) {
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(lvl_ctr, (unsigned long long)total);
+        at = __shfl_sync(FULL, at, 0);
+        if ((long long)(at + total) <= cap_frames) {
+            long long o = (long long)at + incl - nch;
+            for (unsigned m = nch ? mask : 0u; m; m &= m - 1) {
+                const int idx = c_lo + __ffs(m) - 1;
+                const int c = src.ptr ? __ldg(src.ptr + src.base + idx) : idx;
+                const int r = split_child_frames(J, depth, c, Mg);
+                for (int q = 0; q < r; ++q, ++o) {
+                    int32_t *dst = fout + o * sout;
+                    dst[0] = j;
+                    dst[1] = depth + 1;
+                    dst[2] = r == 1 ? -1 : q * SPLIT_RANGE;
+                    dst[3] = r == 1 ? -1 : (q + 1 == r ? 0x7fffffff : (q + 1) * SPLIT_RANGE);
+                    for (int t = 0; t < depth; ++t) dst[FRAME_HDR + t] = Mg[t];
+                    dst[FRAME_HDR + depth] = c;
+                }
+            }
+        } else if (lane == 0) {
+            *(volatile long long *)full = 1;
+        }
+    }
+    // counters: segmented sums over runs of consecutive lanes with the same job
+    const int key = mine ? j : -1;
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || key != prev);
+    const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long a = __shfl_up_sync(FULL, st, o), b = __shfl_up_sync(FULL, nd, o),
+                                 c = __shfl_up_sync(FULL, mt, o), d = __shfl_up_sync(FULL, hs, o);
+        if (lane - o >= head) {
+            st += a;
+            nd += b;
+            mt += c;
+            hs += d;
+        }
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && key >= 0) {
+        unsigned long long *ctr = J.ctr;
+        if (st) atomicAdd(ctr + 1, st);
+        if (nd) atomicAdd(ctr + 2, nd);
+        if (mt) atomicAdd(ctr + 0, mt);
+        if (hs) atomicAdd(ctr + 3, hs);
+    }
+    return longm;
+}
+
 // Single-pass split (unsharded runs; the caller's shard counts the levels).
 // The children of level L are counted on wtot[L] (zeroed by the host).  A
 // level whose children do not all fit is abandoned after its barrier: its
@@ -1345,9 +1512,18 @@ __global__ void __launch_bounds__(BLOCK, 4) k_split_once(const JobDesc *jobs, lo
         const int sin = FRAME_HDR + level, sout = FRAME_HDR + level + 1;
         const long long lo = F * w / nw, hi = F * (w + 1) / nw;
         int longest = 0;
-        for (long long f = lo; f < hi; ++f)
-            longest = max(longest, split_frame_once<DIR>(jobs, fin + f * sin, M, fout, sout, S.cap_ints / sout,
-                                                         lvl_ctr + level, S.result + 5, A));
+        for (long long f0 = lo; f0 < hi; f0 += 32) {
+            // frames of at most 32 candidates one per lane, longer ones a warp at a time
+            unsigned longm = split_lane_frames<DIR>(jobs, fin, f0, hi, level, fout, S.cap_ints / sout,
+                                                    lvl_ctr + level, S.result + 5, longest);
+            while (longm) {
+                const int L = __ffs(longm) - 1;
+                longm &= longm - 1;
+                longest = max(longest, split_frame_once<DIR>(jobs, fin + (f0 + L) * sin, M, fout, sout,
+                                                             S.cap_ints / sout, lvl_ctr + level, S.result + 5, A));
+            }
+        }
+        longest = warp_max(longest);
         if (lane == 0) split_acc_flush(jobs, A);
         if (S.trace && lane == 0 && longest > 0)
             atomicMax(reinterpret_cast<unsigned long long *>(S.trace + KMAX + level), (unsigned long long)longest);
@@ -1788,6 +1964,7 @@ struct CsrJob {
     const int2 *vld;
     const uint64_t *filt, *adj, *hub_bits;
     const BackEdge *back;
+    const PosInfo *pos;
     int n, dw, k, flags;
 };
 
@@ -1832,8 +2009,10 @@ __device__ __forceinline__ bool csr_feasible(const CsrJob &B, const PosC &p, int
             if ((be.dir & 2) && !row_has(B.rowptr, B.col, B.elab, x, c, be.lab_in, chk)) return false;
         }
     }
-    for (int j = 0; j < i; ++j)                                               // rule 1
-        if (M[j] == c) return false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)                                               // rule 1 (same-label positions)
+        for (uint64_t m = B.pos[i].same[h]; m; m &= m - 1)
+            if (M[64 * h + __ffsll((long long)m) - 1] == c) return false;
     return true;
 }
 
@@ -1861,7 +2040,7 @@ __global__ void __launch_bounds__(BLOCK) k_search_csr(const JobDesc *jobs, Searc
             cur_job = fr.job;
             B.rowptr = J.t.rowptr; B.col = J.t.col; B.elab = J.t.elab;
             B.irowptr = J.t.irowptr; B.icol = J.t.icol; B.ielab = J.t.ielab; B.indeg = J.t.indeg;
-            B.ulist = J.ulist; B.vld = J.t.vld; B.filt = J.filt; B.adj = J.t.adj; B.back = J.back;
+            B.ulist = J.ulist; B.vld = J.t.vld; B.filt = J.filt; B.adj = J.t.adj; B.back = J.back; B.pos = J.pos;
             B.hub_slot = J.t.hub_slot; B.hub_bits = J.t.hub_bits;
             B.n = J.t.n; B.dw = J.t.dw; B.k = J.k; B.flags = J.flags;
             for (int t = lane; t < B.k; t += 32) {
