@@ -825,6 +825,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         nverts += jobs[q].p->k;
     }
     const int nf = (int)fjobs.size();
+    if (trace_on()) std::fprintf(stderr, "[sge] %d domain pairs laid out at %.3f ms\n", nf, now_ms() - t_start);
     if (nf > 0) {
         if (nf == nj) {
             CK(upload(W.fjobs, desc, st), "upload domain jobs");   // every job has a filter block
@@ -1076,6 +1077,11 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             build_positions(*J.p, J.mu, J.par, J.algo, J.dsize, J.t->n, jpos[(size_t)q], jback[(size_t)q]);
         }
     }, 64);
+    if (trace_on()) {
+        int act = 0;
+        for (const Job &J : jobs) act += J.active && J.algo != SGE_RI;
+        std::fprintf(stderr, "[sge] RI-DS orderings of %d live pairs built at %.3f ms\n", act, now_ms() - t_start);
+    }
     for (int q = 0; q < nj; ++q) {
         Job &J = jobs[q];
         if (!J.active) continue;
