@@ -741,6 +741,38 @@ def measure_cl100k(E, queries) -> dict:
             "serving": serving}
 
 
+def run_serving(args):
+    """The served query stream at several offered loads: saturation first (all queries
+    submitted at once), then, per load (a fraction of saturation) and run, the Poisson stream
+    of serve_stream; one JSON line per (load, run) with the latency percentiles and parts."""
+    import paper_1705_09358_gb300 as sge
+    from gen import configs
+    pool = spawn_pool()                      # started before the first GPU call
+    queries = cl100k_queries(pool, args.cl100k_queries)
+    pool.close()
+    sge.build.build()
+    E = sge.Context(0)
+    tid = E.load_target(configs.cl100k_target())
+    pids = [E.load_pattern(p) for p in queries]
+    n = len(pids)
+    for _ in range(2):                       # warm the scheduler threads and their workspaces
+        E.serve_submit(tid, pids[0])
+        E.serve_drain()
+    t0 = time.perf_counter()
+    sat = [E.serve_submit(tid, pid) for pid in pids]
+    E.serve_drain()
+    t_sat = time.perf_counter() - t0
+    for tk in sat:
+        E.serve_poll(tk)
+    print(json.dumps({"serving": "saturation", "queries": n, "seconds": t_sat, "qps": n / t_sat}), flush=True)
+    for load in [float(x) for x in args.serving.split(",")]:
+        for run in range(args.serving_runs):
+            lam = load * n / t_sat
+            out = serve_stream(E, tid, pids, lam, configs.cl100k_arrivals(n, lam))
+            print(json.dumps({"serving": "poisson", "load": load, "run": run, **out}), flush=True)
+    E.close()
+
+
 def run_ablation(args):
     """The paper's variant comparison (Section 5: RI-DS vs RI-DS-SI vs RI-DS-SI-FC,
     search-space size and time) re-created on the synthetic workloads; one
@@ -869,9 +901,15 @@ def main():
     ap.add_argument("--workload", default="",
                     help="time one batched workload call by call (er2000, cl10k, cl10k-ri, mol200, cl100k)")
     ap.add_argument("--algo", type=int, default=-1, help="with --workload: the variant (default: the workload's)")
+    ap.add_argument("--serving", default="",
+                    help="comma-separated offered loads (fractions of saturation) for the served cl100k stream")
+    ap.add_argument("--serving-runs", type=int, default=3)
     args = ap.parse_args()
     if args.workload:
         run_workload(args)
+        return
+    if args.serving:
+        run_serving(args)
         return
     if args.ablation:
         run_ablation(args)

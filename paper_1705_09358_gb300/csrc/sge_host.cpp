@@ -339,6 +339,8 @@ struct PatternRec {
     std::vector<int> amat;                 // k x k arc labels, NO_ARC if absent
     std::vector<uint64_t> nb;              // undirected neighbourhood bitsets (2 words per vertex)
     std::vector<int> ri_mu, ri_par;        // cached RI ordering
+    std::vector<PosInfo> ri_pos;           // ... and its position tables (they depend on the pattern alone)
+    std::vector<BackEdge> ri_back;
     // the device arrays, packed into one block (one upload per load) at these
     // int32 offsets, each a multiple of 4 (16-byte aligned)
     DevBuf dall;
@@ -370,16 +372,32 @@ struct PatternRec {
 };
 
 // Scratch of one launch sequence (the serving scheduler has one per slot).
+// One (target, pattern) pair of a batched call, as run_group prepares it.
+struct Job {
+    int pair;        // index into the request
+    TargetRec *t;
+    PatternRec *p;
+    int algo;
+    bool active;
+    long long filt_off = -1;  // offset (u64 words) of the job's filter block
+    long long vert_off = 0;   // offset in the sizes array
+    std::vector<int> mu, par;
+    const long long *dsize = nullptr;   // |D(v)| of the job's pattern vertices (RI-DS), in the workspace
+};
+
 struct Workspace {
     DevBuf jobs, fjobs, ctr, filt, pos, back, ulist, unit_off, vert_off, sizes, task, flag, dent, deoff, vchg, cand,
         ctask;
     DevBuf front[2], counts, offs, scan_tmp, total, splitctl;
     DevBuf pool, pseq, ctl, slab;
     DevBuf mbuf, ckpt, wtrace, smask, plidx, cstart;
+    std::vector<Job> hjobs;       // the call's pairs, reused (their vectors keep their capacity)
     std::vector<JobDesc> hdesc;   // host job records, reused
     std::vector<JobDesc> hfdesc;  // host records of the jobs with a filter block, reused
     std::vector<long long> hsizes;  // host copy of the domain sizes, reused
     std::vector<unsigned long long> hctr;  // host copy of the job counters, reused
+    std::vector<PosInfo> hpos;             // host position tables and back edges, reused
+    std::vector<BackEdge> hback;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;   // search kernel, split kernel
     cudaStream_t bound = nullptr;
 #define SGE_WS_BUFFERS                                                                                             \
@@ -627,17 +645,6 @@ void build_positions(const PatternRec &P, const std::vector<int> &mu, const std:
     back.resize(nb);
 }
 
-struct Job {
-    int pair;        // index into the request
-    TargetRec *t;
-    PatternRec *p;
-    int algo;
-    bool active;
-    long long filt_off = -1;  // offset (u64 words) of the job's filter block
-    long long vert_off = 0;   // offset in the sizes array
-    std::vector<int> mu, par;
-    const long long *dsize = nullptr;   // |D(v)| of the job's pattern vertices (RI-DS), in the workspace
-};
 
 struct PairReq {
     int32_t tid, pid;
@@ -706,11 +713,15 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     long long launches = 0;   // kernels launched by this call
     const int algo = o.algo;
     const int nj = (int)idx.size();
-    std::vector<Job> jobs(nj);
+    std::vector<Job> &jobs = W.hjobs;   // kept across calls (no fresh pages)
+    if (jobs.size() < (size_t)nj) jobs.resize((size_t)nj);
     bool directed = false, any_elab = false;
     int kmax = 1, nmax = 1;
     for (int q = 0; q < nj; ++q) {
         Job &J = jobs[q];
+        J.filt_off = -1;
+        J.vert_off = 0;
+        J.dsize = nullptr;
         J.pair = idx[q];
         J.t = reqs[J.pair].t;
         J.p = reqs[J.pair].p;
@@ -733,8 +744,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     // shared memory
     bool bits_ok = !directed && !any_elab;
     int nwl = 1;
-    for (const Job &J : jobs)
-        if (J.active) {
+    for (int q = 0; q < nj; ++q)   // (the workspace's job vector may be longer than this call)
+        if (const Job &J = jobs[q]; J.active) {
             if (!J.t->adj.p) bits_ok = false;
             nwl = std::max(nwl, pow2_at_least((J.t->dw + 31) / 32));
         }
@@ -752,7 +763,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     // ---------------------------------------------------------- job tables
     long long filt_words = 0, nverts = 0, nunits = 0;
     std::vector<long long> unit_off, vert_off;
-    for (Job &J : jobs) {
+    for (int q = 0; q < nj; ++q) {
+        Job &J = jobs[q];
         if (!J.active) continue;
         if (J.algo != SGE_RI || need_filt_all) {
             J.filt_off = filt_words;
@@ -1054,8 +1066,10 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     // orderings and position tables; RI tables depend only on the pattern and
     // are shared by every job of that pattern (n_t of an unparented RI position
     // is read from the job's target at run time)
-    std::vector<PosInfo> pos;
-    std::vector<BackEdge> back;
+    std::vector<PosInfo> &pos = W.hpos;     // kept across calls (no fresh pages)
+    std::vector<BackEdge> &back = W.hback;
+    pos.clear();
+    back.clear();
     std::vector<long long> pos_off(nj, 0), back_off(nj, 0);
     std::vector<int> task_job, task_vert, task_out;
     std::vector<int> fidx(nj, -1);
@@ -1063,8 +1077,6 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     std::unordered_map<const PatternRec *, std::pair<long long, long long>> ri_tables;
     ri_tables.reserve(64);
     long long ulist_len = 0;
-    std::vector<PosInfo> pq;
-    std::vector<BackEdge> bq;
     // the RI-DS jobs' orderings and tables (each depends on its own domain sizes) on a few host
     // threads, into per-job vectors; they are appended in job order below
     std::vector<std::vector<PosInfo>> jpos((size_t)nj);
@@ -1079,7 +1091,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     }, 64);
     if (trace_on()) {
         int act = 0;
-        for (const Job &J : jobs) act += J.active && J.algo != SGE_RI;
+        for (int q = 0; q < nj; ++q) act += jobs[q].active && jobs[q].algo != SGE_RI;
         std::fprintf(stderr, "[sge] RI-DS orderings of %d live pairs built at %.3f ms\n", act, now_ms() - t_start);
     }
     for (int q = 0; q < nj; ++q) {
@@ -1089,9 +1101,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             auto it = ri_tables.find(J.p);
             if (it == ri_tables.end()) {
                 const long long po = (long long)pos.size(), bo = (long long)back.size();
-                build_positions(*J.p, J.p->ri_mu, J.p->ri_par, SGE_RI, nullptr, 0, pq, bq);
-                pos.insert(pos.end(), pq.begin(), pq.end());
-                back.insert(back.end(), bq.begin(), bq.end());
+                pos.insert(pos.end(), J.p->ri_pos.begin(), J.p->ri_pos.end());
+                back.insert(back.end(), J.p->ri_back.begin(), J.p->ri_back.end());
                 it = ri_tables.emplace(J.p, std::make_pair(po, bo)).first;
             }
             pos_off[q] = it->second.first;
@@ -2131,6 +2142,7 @@ sge_status sge_load_pattern(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *s
             P->nb[2 * w + (v >> 6)] |= 1ull << (v & 63);
         }
     gcf_order(*P, SGE_RI, nullptr, P->ri_mu, P->ri_par);
+    build_positions(*P, P->ri_mu, P->ri_par, SGE_RI, nullptr, 0, P->ri_pos, P->ri_back);
     std::vector<int32_t> img;   // the host image of P->dall
     auto put = [&img](const std::vector<int32_t> &v) {
         const size_t at = img.size();
