@@ -241,7 +241,7 @@ void sge_free(void *p);
 
 /* Serving (continuous batching).  sge_serve_submit queues one query and
  * returns at once with a ticket; scheduler threads owned by the context
- * admit every queued query (up to 512, within a device-memory budget) into
+ * admit queued queries (up to 64, within a device-memory budget) into
  * the next free launch slot, and each slot runs its admitted group through
  * the batched launch sequence on its own stream, so a group's host work and
  * launches overlap with earlier groups still on the device.

@@ -2509,7 +2509,7 @@ const char *sge_last_error(sge_ctx *ctx) {
 namespace {
 
 constexpr int SERVE_SLOTS = 4;               // concurrent launch groups (one stream each)
-constexpr int SERVE_GROUP_MAX = 512;         // queries admitted into one launch
+constexpr int SERVE_GROUP_MAX = 64;          // queries admitted into one launch (a group ends with its slowest query)
 constexpr long long SERVE_BYTES = 2ll << 30; // device memory budget for admitted queries
 
 long long query_bytes(const TargetRec &t, const PatternRec &p) {
