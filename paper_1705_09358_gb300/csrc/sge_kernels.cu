@@ -262,62 +262,77 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init_buckets(const JobDesc *jo
     }
 }
 
-constexpr int INIT_WORDS_PER_WARP = 32;   // consecutive filter words one warp of k_domain_init writes
+constexpr int INIT_WORDS_PER_WARP = 32;   // most consecutive filter words one warp of k_domain_init writes
 
 __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
-                                                       long long nunits) {
-    const long long u0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * INIT_WORDS_PER_WARP;
+                                                       long long nunits, int wpw) {
+    const long long u0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * wpw;
     const int lane = threadIdx.x & 31;
     if (u0 >= nunits) return;
     // the warp's words are consecutive units: find the job once, then step over its
     // boundaries; (v, q) = (pattern vertex, word) steps along with u (a job holds
-    // k x dw < 2^15 units, so 32-bit arithmetic)
+    // k x dw < 2^15 units, so 32-bit arithmetic).  The job's fields are read once per job
+    // and the vertex's once per vertex, not once per word.
     int j = find_job(unit_off, njobs, u0);
-    int v = -1, q = 0;
-    for (long long u = u0; u < u0 + INIT_WORDS_PER_WARP && u < nunits; ++u) {
-        bool moved = false;
-        while (j + 1 < njobs && unit_off[j + 1] <= u) {
-            ++j;
-            moved = true;
-        }
+    int jcur = -1, v = -1, q = 0, vcur = -1;
+    bool skip = true, DIR = false, nbcheck = false;
+    int dw = 1, n = 0, lab = 0, od = 0, id = 0;
+    const int2 *vld = nullptr;
+    const int32_t *indeg = nullptr;
+    uint64_t *filt = nullptr;
+    for (long long u = u0; u < u0 + wpw && u < nunits; ++u) {
+        while (j + 1 < njobs && unit_off[j + 1] <= u) ++j;
         const JobDesc &J = jobs[j];
-        if (v < 0 || moved) {
+        if (j != jcur) {
+            jcur = j;
+            skip = J.filt == nullptr || J.t.lbuck != nullptr;   // (bucket targets: k_domain_init_buckets)
+            DIR = (J.flags & JOB_DIRECTED) != 0;
+            // RI-DS on an undirected target without edge labels: a candidate t also needs, for
+            // every pattern neighbour u of v, a neighbour of its own with u's label and at least
+            // u's degree.  That is arc consistency's test against the domains as initialised, so
+            // dropping the failures here removes only candidates the first sweep would remove;
+            // their rows, which the sweep would scan to the end, are never read.
+            nbcheck = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && !DIR && J.t.nbmax != nullptr &&
+                      J.plidx != nullptr;
+            dw = J.t.dw;
+            n = J.t.n;
+            vld = J.t.vld;
+            indeg = J.t.indeg;
+            filt = J.filt;
             const int local = (int)(u - unit_off[j]);
-            v = local / J.t.dw;
-            q = local - v * J.t.dw;
-        } else if (++q == J.t.dw) {
+            v = local / dw;
+            q = local - v * dw;
+            vcur = -1;
+        } else if (++q == dw) {
             q = 0;
             ++v;
         }
-        if (J.filt == nullptr || J.t.lbuck != nullptr) continue;   // (bucket targets: k_domain_init_buckets)
-        const bool DIR = (J.flags & JOB_DIRECTED) != 0;
-        const int lab = J.p.lab[v], od = J.p.odeg[v], id = DIR ? J.p.ideg[v] : 0;
-        // RI-DS on an undirected target without edge labels: a candidate t also needs, for every
-        // pattern neighbour u of v, a neighbour of its own with u's label and at least u's degree.
-        // That is arc consistency's test against the domains as initialised, so dropping the
-        // failures here removes only candidates the first sweep would remove; their rows, which
-        // the sweep would scan to the end, are never read.
-        const bool nbcheck = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && !DIR && J.t.nbmax != nullptr &&
-                             J.plidx != nullptr;
+        if (skip) continue;
+        if (v != vcur) {
+            vcur = v;
+            lab = J.p.lab[v];
+            od = J.p.odeg[v];
+            id = DIR ? J.p.ideg[v] : 0;
+        }
         unsigned long long word = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int t = q * 64 + h * 32 + lane;
             bool ok = false;
-            if (t < J.t.n) {
-                const int2 x = __ldg(J.t.vld + t);
-                ok = x.x == lab && x.y >= od && (!DIR || __ldg(J.t.indeg + t) >= id);
+            if (t < n) {
+                const int2 x = __ldg(vld + t);
+                ok = x.x == lab && x.y >= od && (!DIR || __ldg(indeg + t) >= id);
             }
             if (nbcheck && __any_sync(FULL, ok)) {
                 for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) {
                     const int pu = J.p.col[e];
                     const int li = J.plidx[pu];   // lab(pu)'s index among the target's labels, -1 if absent
-                    if (ok) ok = li >= 0 && __ldg(J.t.nbmax + (size_t)li * J.t.n + t) >= J.p.odeg[pu];
+                    if (ok) ok = li >= 0 && __ldg(J.t.nbmax + (size_t)li * n + t) >= J.p.odeg[pu];
                 }
             }
             word |= (unsigned long long)__ballot_sync(FULL, ok) << (32 * h);
         }
-        if (lane == 0) J.filt[(size_t)v * J.t.dw + q] = word;
+        if (lane == 0) filt[(size_t)v * dw + q] = word;
     }
 }
 
@@ -2816,8 +2831,15 @@ cudaError_t launch_label_index(const JobDesc *jobs, const long long *vert_off, i
 cudaError_t launch_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs, long long nunits,
                                cudaStream_t st) {
     if (nunits <= 0) return cudaSuccess;
-    k_domain_init<<<grid_for((nunits + INIT_WORDS_PER_WARP - 1) / INIT_WORDS_PER_WARP), BLOCK, 0, st>>>(
-        jobs, unit_off, njobs, nunits);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // words per warp: up to 32 (a warp steps along its words reading each job's and vertex's
+    // fields once), fewer when that would leave the device short of warps (64 per SM)
+    const long long want = nunits / ((long long)sms * 64);
+    const int wpw = (int)std::max<long long>(1, std::min<long long>(INIT_WORDS_PER_WARP, want));
+    k_domain_init<<<grid_for((nunits + wpw - 1) / wpw), BLOCK, 0, st>>>(jobs, unit_off, njobs, nunits, wpw);
     return cudaGetLastError();
 }
 
