@@ -997,7 +997,19 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
                         if (dirty[(size_t)g]) {
                             const int fj = gjob[(size_t)g];
                             if (cand_mode && csize[(size_t)g] == 0) continue;
-                            ent.push_back(make_int4(fj, gv_v[(size_t)g], (int)g, (int)cstart[(size_t)g]));
+                            int ey = gv_v[(size_t)g];
+                            if (cand_mode) {
+                                // every pattern neighbour's domain (as first counted) is dense: the
+                                // sweep lets a lane try a long row before the warp
+                                const Job &Jq = jobs[fjobs[fj]];
+                                bool dense = true;
+                                for (int w = 0; w < 2 && dense; ++w)
+                                    for (uint64_t b = Jq.p->nb[(size_t)ey * 2 + w]; b && dense; b &= b - 1)
+                                        dense = csize[(size_t)Jq.vert_off + 64 * w + __builtin_ctzll(b)] * AC_DENSE >=
+                                                Jq.t->n;
+                                if (dense) ey |= AC_ENT_DENSE;
+                            }
+                            ent.push_back(make_int4(fj, ey, (int)g, (int)cstart[(size_t)g]));
                             eoff.push_back(units);
                             units += cand_mode ? csize[(size_t)g] : jobs[fjobs[fj]].t->dw;
                         }

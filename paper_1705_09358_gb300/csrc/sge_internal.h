@@ -38,6 +38,10 @@ constexpr int JOB_RIDS = 1;          // test v_t in D(mu_i) for every candidate
 constexpr int JOB_ELAB = 2;          // compare edge labels
 constexpr int JOB_DIRECTED = 4;
 constexpr int JOB_FC = 8;            // forward checking of singleton domains
+// Arc-consistency sweep entries {job, pattern vertex (| AC_ENT_DENSE), global vertex, list start}:
+// AC_ENT_DENSE marks a vertex whose pattern neighbours' domains are all dense (see k_domain_ac_cand)
+constexpr int AC_ENT_DENSE = 1 << 16;
+constexpr int AC_DENSE = 8;           // dense: a domain holding at least 1/AC_DENSE of the target
 constexpr int JOB_LONG_LISTS = 16;   // some position after the first may have more than SPLIT_RANGE candidates
 
 // The breadth-first split writes a child whose candidate list is longer than

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
 // Arc consistency of one candidate (Section 4): does target vertex t keep,
 // for every pattern edge at v, a compatible target edge into the other
 // endpoint's domain?
-__device__ bool ac_supported(const JobDesc &J, int v, int t, bool DIR, bool chk) {
+__device__ __forceinline__ bool ac_supported(const JobDesc &J, int v, int t, bool DIR, bool chk) {
     const int dw = J.t.dw;
     for (int e = J.p.rowptr[v]; e < J.p.rowptr[v + 1]; ++e) {
         const int uu = J.p.col[e], bl = chk ? J.p.elab[e] : 0;
@@ -369,7 +369,7 @@ __device__ bool ac_supported(const JobDesc &J, int v, int t, bool DIR, bool chk)
 // Warp-collective form of ac_supported for a candidate with a long row: for each
 // pattern edge the 32 lanes stride t's row and a ballot says whether any of them
 // found a compatible neighbour in the other endpoint's domain.
-__device__ bool ac_supported_warp(const JobDesc &J, int v, int t, bool DIR, bool chk) {
+__device__ __forceinline__ bool ac_supported_warp(const JobDesc &J, int v, int t, bool DIR, bool chk) {
     const int lane = threadIdx.x & 31;
     const int dw = J.t.dw;
     for (int pass = 0; pass < (DIR ? 2 : 1); ++pass) {
@@ -399,26 +399,84 @@ __device__ bool ac_supported_warp(const JobDesc &J, int v, int t, bool DIR, bool
     return true;
 }
 
-// Rows longer than this are searched by the whole warp (ac_supported_warp).
+// A candidate whose row (out- plus in-row) is longer than AC_WARP_ROW is searched
+// by the whole warp (ac_supported_warp) -- unless the domains at the other ends of
+// its pattern edges are dense (each at least 1/AC_DENSE of the target), where a
+// row scan finds support within a few entries: then its own lane scans at most
+// AC_LANE_SCAN entries per pattern edge first, and only an edge left open sends
+// it to the warp.  Rows longer than AC_WARP_ROW_DIRECT always go to the warp.
 constexpr int AC_WARP_ROW = 48;
+constexpr int AC_LANE_SCAN = 32;
+constexpr int AC_WARP_ROW_DIRECT = 512;
+
+// ac_supported with each row scan cut after `bound` entries: returns false if
+// some pattern edge has no support (its whole row scanned), true if every edge
+// found one, and sets `open` (result then true) when no edge failed but some
+// scan stopped at the bound.
+__device__ __forceinline__ bool ac_supported_bounded(const JobDesc &J, int v, int t, bool DIR, bool chk, int bound, bool &open) {
+    const int dw = J.t.dw;
+    open = false;
+    for (int pass = 0; pass < (DIR ? 2 : 1); ++pass) {
+        const int32_t *prow = pass ? J.p.irowptr : J.p.rowptr;
+        const int32_t *pcol = pass ? J.p.icol : J.p.col;
+        const int32_t *pel = pass ? J.p.ielab : J.p.elab;
+        const int32_t *trow = pass ? J.t.irowptr : J.t.rowptr;
+        const int32_t *tcol = pass ? J.t.icol : J.t.col;
+        const int32_t *tel = pass ? J.t.ielab : J.t.elab;
+        const int f0 = __ldg(trow + t), fe = __ldg(trow + t + 1);
+        const int fb = min(fe, f0 + bound);
+        for (int e = prow[v]; e < prow[v + 1]; ++e) {
+            const int uu = pcol[e], bl = chk ? pel[e] : 0;
+            const uint64_t *Du = J.filt + (size_t)uu * dw;
+            bool found = false;
+            for (int f = f0; f < fb; ++f) {
+                const int y = __ldg(tcol + f);
+                if ((!chk || __ldg(tel + f) == bl) && ((Du[y >> 6] >> (y & 63)) & 1ull)) { found = true; break; }
+            }
+            if (!found) {
+                if (fb == fe) return false;
+                open = true;
+            }
+        }
+    }
+    return true;
+}
+
+// Lane-local part of the arc-consistency test of candidate t of D(v) with a row of
+// `len` entries: whether to drop it, or (`heavy`) to leave it to the warp.
+__device__ __forceinline__ bool ac_lane_check(const JobDesc &J, int v, int t, bool DIR, bool chk, int len,
+                                              bool dense, bool &heavy) {
+    heavy = false;
+    if (len <= AC_WARP_ROW) return !ac_supported(J, v, t, DIR, chk);
+    if (!dense || len > AC_WARP_ROW_DIRECT) {
+        heavy = true;
+        return false;
+    }
+    bool open = false;
+    const bool sup = ac_supported_bounded(J, v, t, DIR, chk, AC_LANE_SCAN, open);
+    heavy = open;
+    return !sup;
+}
 
 // The same sweep over explicit candidate lists: one lane per listed candidate of
 // the listed entries {job, pattern vertex, global vertex, list start}; a removed
 // candidate is cleared from D(v) and its list slot.  A lane tests a candidate with
 // a short row itself; the warp then takes its lanes' long-row candidates one at a
 // time together, so a hub's row is read 32 entries per step instead of one.
-__global__ void __launch_bounds__(BLOCK) k_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff,
+__global__ void __launch_bounds__(BLOCK, 1) k_domain_ac_cand(const JobDesc *jobs, const int4 *ent, const long long *eoff,
                                                           int nent, long long ncand, int32_t *cand, int *changed,
                                                           unsigned char *vchanged) {
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if ((x & ~31ll) >= ncand) return;   // warp-uniform: a warp with any candidate stays whole
     const int lane = threadIdx.x & 31;
     int jidx = 0, v = 0, g = 0, t = -1;
+    bool dense_v = false;
     int32_t *slot = nullptr;
     if (x < ncand) {
         const int i = find_job(eoff, nent, x);
         const int4 E = ent[i];
-        jidx = E.x; v = E.y; g = E.z;
+        jidx = E.x; v = E.y & (AC_ENT_DENSE - 1); g = E.z;
+        dense_v = (E.y & AC_ENT_DENSE) != 0;
         slot = cand + (long long)E.w + (x - eoff[i]);
         t = *slot;
     }
@@ -432,8 +490,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_ac_cand(const JobDesc *jobs, c
             const bool DIR = (J.flags & JOB_DIRECTED) != 0;
             const int len = __ldg(J.t.rowptr + t + 1) - __ldg(J.t.rowptr + t) +
                             (DIR ? __ldg(J.t.irowptr + t + 1) - __ldg(J.t.irowptr + t) : 0);
-            heavy = len > AC_WARP_ROW;
-            drop = !heavy && !ac_supported(J, v, t, DIR, (J.flags & JOB_ELAB) != 0);
+            drop = ac_lane_check(J, v, t, DIR, (J.flags & JOB_ELAB) != 0, len, dense_v, heavy);
         }
     }
     unsigned hv = __ballot_sync(FULL, heavy);
@@ -461,7 +518,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_ac_cand(const JobDesc *jobs, c
 // the listed (job, pattern vertex) entries -- those with a neighbour whose
 // domain shrank in the previous sweep -- one warp per 64-target word, and
 // marks every domain it shrinks in vchanged.
-__global__ void __launch_bounds__(BLOCK) k_domain_ac(const JobDesc *jobs, const int4 *ent, const long long *eoff,
+__global__ void __launch_bounds__(BLOCK, 1) k_domain_ac(const JobDesc *jobs, const int4 *ent, const long long *eoff,
                                                      int nent, long long nunits, int *changed,
                                                      unsigned char *vchanged) {
     const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -472,7 +529,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_ac(const JobDesc *jobs, const 
     const JobDesc &J = jobs[E.x];
     if (J.filt == nullptr || !(J.flags & JOB_RIDS)) return;
     const bool DIR = (J.flags & JOB_DIRECTED) != 0;
-    const int v = E.y, q = (int)(u - eoff[i]);
+    const int v = E.y & (AC_ENT_DENSE - 1), q = (int)(u - eoff[i]);
     uint64_t *wp = J.filt + (size_t)v * J.t.dw + q;
     const uint64_t word = *wp;
     if (word == 0) return;
@@ -647,7 +704,7 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const
                                                                         const long long *vert_off,
                                                            const long long *cstart, const long long *csize,
                                                            int32_t *cand, int *next_job) {
-    __shared__ unsigned char dirty[KMAX], chg[KMAX], done[KMAX];
+    __shared__ unsigned char dirty[KMAX], chg[KMAX], done[KMAX], dns[KMAX];
     __shared__ int dl[KMAX], size[KMAX], elem[KMAX], newu[KMAX];
     __shared__ long long pre[KMAX + 1];
     __shared__ int nd, any, nnew, empty;
@@ -743,6 +800,16 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const
                     }
                 } else {
                     const long long g0 = vert_off[jb];
+                    // dense: every pattern neighbour's domain holds at least 1/AC_DENSE of the target
+                    for (int i = tid; i < n_d; i += blockDim.x) {
+                        const int dv = dl[i];
+                        bool d = true;
+                        for (int e = J.p.rowptr[dv]; d && e < J.p.rowptr[dv + 1]; ++e)
+                            d = (long long)size[J.p.col[e]] * AC_DENSE >= J.t.n;
+                        for (int e = DIR ? J.p.irowptr[dv] : 0; d && DIR && e < J.p.irowptr[dv + 1]; ++e)
+                            d = (long long)size[J.p.icol[e]] * AC_DENSE >= J.t.n;
+                        dns[dv] = d;
+                    }
                     if (tid == 0) {
                         long long acc = 0;
                         for (int i = 0; i < n_d; ++i) {
@@ -774,8 +841,7 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const
                             } else {
                                 const int len = __ldg(J.t.rowptr + t + 1) - __ldg(J.t.rowptr + t) +
                                                 (DIR ? __ldg(J.t.irowptr + t + 1) - __ldg(J.t.irowptr + t) : 0);
-                                heavy = len > AC_WARP_ROW;
-                                drop = !heavy && !ac_supported(J, v, t, DIR, chk);
+                                drop = ac_lane_check(J, v, t, DIR, chk, len, dns[v] != 0, heavy);
                             }
                         }
                         unsigned hv = __ballot_sync(FULL, heavy);
