@@ -70,7 +70,7 @@ typedef struct {
     int32_t algo;              /* SGE_RI .. SGE_RIDS_SI_FC (default SGE_RI) */
     int32_t split_depth;       /* depth of the breadth-first split; 0 = auto */
     int32_t frames_per_warp;   /* auto split stops at frames_per_warp x resident warps (default 8) */
-    int32_t steal_granularity; /* most frames one donation hands out (default 16 for the bitset
+    int32_t steal_granularity; /* most frames one donation hands out (default 32 for the bitset
                                   kernel, 2 for the CSR kernel) */
     int64_t state_budget;      /* stop after about this many states of one pair (0 = none) */
     int64_t time_limit_ms;     /* stop after about this much search-kernel time (0 = none);

@@ -1380,7 +1380,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         C.donate = o.no_donation ? 0 : 1;
         // a bitset-kernel donor hands out up to 16 of its shallowest pending survivors at once:
         // with few, large frontier frames the tail is split fastest that way
-        C.gran = o.steal_granularity > 0 ? o.steal_granularity : (kernel == SGE_KERNEL_BITSET ? 16 : 2);
+        C.gran = o.steal_granularity > 0 ? o.steal_granularity : (kernel == SGE_KERNEL_BITSET ? 32 : 2);
         // donation cadence: a busy warp checks whether idle warps wait for work at most once
         // per this many iterations or this much device time.  Donating costs a few microseconds
         // (two fetch-and-adds and one cell write), so the bitset kernel checks every 50 us; the
