@@ -398,6 +398,9 @@ struct Workspace {
     std::vector<unsigned long long> hctr;  // host copy of the job counters, reused
     std::vector<PosInfo> hpos;             // host position tables and back edges, reused
     std::vector<BackEdge> hback;
+    std::vector<std::vector<PosInfo>> hjpos;   // per job: its RI-DS position tables, reused
+    std::vector<std::vector<BackEdge>> hjback;
+    std::vector<long long> hri_off;        // per pattern id: offsets of its RI tables in this call
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;   // search kernel, split kernel
     cudaStream_t bound = nullptr;
 #define SGE_WS_BUFFERS                                                                                             \
@@ -717,28 +720,37 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     if (jobs.size() < (size_t)nj) jobs.resize((size_t)nj);
     bool directed = false, any_elab = false;
     int kmax = 1, nmax = 1;
-    for (int q = 0; q < nj; ++q) {
-        Job &J = jobs[q];
-        J.filt_off = -1;
-        J.vert_off = 0;
-        J.dsize = nullptr;
-        J.pair = idx[q];
-        J.t = reqs[J.pair].t;
-        J.p = reqs[J.pair].p;
-        if (!J.t || !J.p) {
-            std::lock_guard<std::mutex> g(ctx->mu);
-            J.t = ctx->targets.at(reqs[J.pair].tid).get();
-            J.p = ctx->patterns.at(reqs[J.pair].pid).get();
+    std::mutex red;   // merges the threads' partial maxima
+    parallel_for(nj, [&](int q0, int q1) {
+        bool el = false;
+        int km = 1, nm = 1;
+        for (int q = q0; q < q1; ++q) {
+            Job &J = jobs[q];
+            J.filt_off = -1;
+            J.vert_off = 0;
+            J.dsize = nullptr;
+            J.pair = idx[q];
+            J.t = reqs[J.pair].t;
+            J.p = reqs[J.pair].p;
+            if (!J.t || !J.p) {
+                std::lock_guard<std::mutex> g(ctx->mu);
+                J.t = ctx->targets.at(reqs[J.pair].tid).get();
+                J.p = ctx->patterns.at(reqs[J.pair].pid).get();
+            }
+            J.algo = algo;
+            J.active = J.p->k > 0 && J.p->k <= J.t->n;
+            if (J.active) {
+                km = std::max(km, J.p->k);
+                nm = std::max(nm, J.t->n);
+                el = el || J.t->any_elab || J.p->any_elab;
+            }
         }
-        J.algo = algo;
-        J.active = J.p->k > 0 && J.p->k <= J.t->n;
-        directed = J.t->directed;
-        if (J.active) {
-            kmax = std::max(kmax, J.p->k);
-            nmax = std::max(nmax, J.t->n);
-            any_elab = any_elab || J.t->any_elab || J.p->any_elab;
-        }
-    }
+        std::lock_guard<std::mutex> g(red);
+        kmax = std::max(kmax, km);
+        nmax = std::max(nmax, nm);
+        any_elab = any_elab || el;
+    });
+    if (nj > 0) directed = jobs[0].t->directed;   // (a group holds pairs of one directedness)
     // kernel family: the bitset kernel needs undirected, unlabelled edges, an
     // adjacency bitset and at most 4 words per lane with the level stack in
     // shared memory
@@ -1086,13 +1098,23 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     std::vector<int> task_job, task_vert, task_out;
     std::vector<int> fidx(nj, -1);
     for (int x = 0; x < nf; ++x) fidx[fjobs[x]] = x;
-    std::unordered_map<const PatternRec *, std::pair<long long, long long>> ri_tables;
-    ri_tables.reserve(64);
+    // an RI pattern's tables are appended once per call: their offsets, by pattern id
+    int max_pid = 0;
+    for (int q = 0; q < nj; ++q) max_pid = std::max(max_pid, reqs[jobs[q].pair].pid);
+    std::vector<long long> &ri_off = W.hri_off;   // [pid]: pos offset, back offset (-1: not yet)
+    if (ri_off.size() < 2 * ((size_t)max_pid + 1)) ri_off.resize(2 * ((size_t)max_pid + 1), -1);
+    std::vector<int> ri_seen;
     long long ulist_len = 0;
     // the RI-DS jobs' orderings and tables (each depends on its own domain sizes) on a few host
-    // threads, into per-job vectors; they are appended in job order below
-    std::vector<std::vector<PosInfo>> jpos((size_t)nj);
-    std::vector<std::vector<BackEdge>> jback((size_t)nj);
+    // threads, into per-job vectors (kept in the workspace); they are appended in job order below
+    std::vector<std::vector<PosInfo>> &jpos = W.hjpos;
+    std::vector<std::vector<BackEdge>> &jback = W.hjback;
+    bool any_rids_job = false;
+    for (int q = 0; q < nj && !any_rids_job; ++q) any_rids_job = jobs[q].active && jobs[q].algo != SGE_RI;
+    if (any_rids_job && jpos.size() < (size_t)nj) {
+        jpos.resize((size_t)nj);
+        jback.resize((size_t)nj);
+    }
     parallel_for(nj, [&](int q0, int q1) {
         for (int q = q0; q < q1; ++q) {
             Job &J = jobs[q];
@@ -1110,15 +1132,16 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         Job &J = jobs[q];
         if (!J.active) continue;
         if (J.algo == SGE_RI) {
-            auto it = ri_tables.find(J.p);
-            if (it == ri_tables.end()) {
-                const long long po = (long long)pos.size(), bo = (long long)back.size();
+            const size_t pid = (size_t)reqs[J.pair].pid;
+            if (ri_off[2 * pid] < 0) {
+                ri_off[2 * pid] = (long long)pos.size();
+                ri_off[2 * pid + 1] = (long long)back.size();
                 pos.insert(pos.end(), J.p->ri_pos.begin(), J.p->ri_pos.end());
                 back.insert(back.end(), J.p->ri_back.begin(), J.p->ri_back.end());
-                it = ri_tables.emplace(J.p, std::make_pair(po, bo)).first;
+                ri_seen.push_back((int)pid);
             }
-            pos_off[q] = it->second.first;
-            back_off[q] = it->second.second;
+            pos_off[q] = ri_off[2 * pid];
+            back_off[q] = ri_off[2 * pid + 1];
             continue;
         }
         pos_off[q] = (long long)pos.size();
@@ -1138,6 +1161,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         pos.insert(pos.end(), pq.begin(), pq.end());
         back.insert(back.end(), bq.begin(), bq.end());
     }
+    for (int pid : ri_seen) ri_off[2 * (size_t)pid] = ri_off[2 * (size_t)pid + 1] = -1;
     if (ulist_len > INT32_MAX) return fail(ctx, SGE_ERR_OOM, "unparented candidate lists too large");
     if (trace_on())
         std::fprintf(stderr,
@@ -1204,6 +1228,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     // when the root has more (a range frame counts the node's states only if it
     // starts at candidate 0)
     std::vector<std::array<int32_t, 4>> roots;
+    roots.reserve((size_t)nj);
     for (int q = 0; q < nj; ++q) {
         const Job &J = jobs[q];
         if (!J.active) continue;
@@ -1601,19 +1626,31 @@ sge_status prepare_pairs(sge_ctx *ctx, std::vector<PairReq> &reqs, const sge_opt
     dir.clear();
     {
         std::lock_guard<std::mutex> g(ctx->mu);
-        int last_tid = 0, last_pid = 0;   // consecutive pairs often repeat an id
-        TargetRec *T = nullptr;
-        PatternRec *P = nullptr;
+        // ids are handed out in sequence, so a call resolves each distinct id once through the
+        // maps and every pair through a table indexed by id (large batches repeat few ids)
+        std::vector<TargetRec *> tt((size_t)std::max(ctx->next_target, 1), nullptr);
+        std::vector<PatternRec *> pt((size_t)std::max(ctx->next_pattern, 1), nullptr);
+        std::vector<unsigned char> tseen(tt.size(), 0), pseen(pt.size(), 0);
+        und.reserve(reqs.size());
         for (size_t i = 0; i < reqs.size(); ++i) {
-            if (!T || reqs[i].tid != last_tid) {
-                auto ti = ctx->targets.find(reqs[i].tid);
-                T = ti == ctx->targets.end() ? nullptr : ti->second.get();
-                last_tid = reqs[i].tid;
+            const int32_t tid = reqs[i].tid, pid = reqs[i].pid;
+            TargetRec *T = nullptr;
+            PatternRec *P = nullptr;
+            if (tid >= 0 && (size_t)tid < tt.size()) {
+                if (!tseen[(size_t)tid]) {
+                    auto ti = ctx->targets.find(tid);
+                    tt[(size_t)tid] = ti == ctx->targets.end() ? nullptr : ti->second.get();
+                    tseen[(size_t)tid] = 1;
+                }
+                T = tt[(size_t)tid];
             }
-            if (!P || reqs[i].pid != last_pid) {
-                auto pi = ctx->patterns.find(reqs[i].pid);
-                P = pi == ctx->patterns.end() ? nullptr : pi->second.get();
-                last_pid = reqs[i].pid;
+            if (pid >= 0 && (size_t)pid < pt.size()) {
+                if (!pseen[(size_t)pid]) {
+                    auto pi = ctx->patterns.find(pid);
+                    pt[(size_t)pid] = pi == ctx->patterns.end() ? nullptr : pi->second.get();
+                    pseen[(size_t)pid] = 1;
+                }
+                P = pt[(size_t)pid];
             }
             if (!T || !P) {
                 ctx->err = "unknown target or pattern id";
