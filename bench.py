@@ -250,7 +250,9 @@ def search_roofline(kernel_s: float, alg_bytes: float, nodes: float, sm_mhz, sms
 
     The kernel's data (adjacency bitset, domains, frames) is L2-resident, so
     DRAM moves a few MB per launch while the algorithmic bytes are ~14 GB; the
-    binding resource is instruction issue.  achieved = warp instructions of one
+    nearest hardware ceiling is instruction issue (what keeps the kernel below
+    it is the latency of the L2-resident row loads with half the warp slots
+    resident, and the idle tail of the search).  achieved = warp instructions of one
     launch (ncu count of the current sources) / the live CUDA-event time of one
     launch; peak = SMs x 4 schedulers x 1 warp instruction per cycle x the
     median SM clock sampled in the timed region.  The bytes-based figures stay
@@ -263,7 +265,9 @@ def search_roofline(kernel_s: float, alg_bytes: float, nodes: float, sm_mhz, sms
     mhz = float(sm_mhz) if sm_mhz else 2070.0
     peak = sms * WARP_SCHEDULERS_PER_SM * mhz * 1e6
     alg_gbs = alg_bytes / kernel_s / 1e9
-    out = {"bound": "alu", "limiter": "warp-instruction issue (data L2-resident)",
+    out = {"bound": "alu",
+           "limiter": "warp-instruction issue is the nearest ceiling; below it: latency of L2-resident row "
+                      "loads (half the warp slots resident) and the search's idle tail",
            "achieved": inst / kernel_s if inst else None, "peak": peak, "unit": "warp instructions/s",
            "frac": inst / kernel_s / peak if inst else None, "traffic": traffic,
            "kernel": "k_search_bits<1> (persistent bitset search)", "kernel_ms_per_launch": kernel_s * 1e3,
