@@ -1009,7 +1009,7 @@ __global__ void __launch_bounds__(BLOCK) k_split(const JobDesc *jobs, const int3
         __syncwarp();
         const int k = J.k;
         const bool leaf = depth + 1 == k;
-        const PosInfo P = J.pos[depth];
+        const PosInfo &P = J.pos[depth];
         const Src S = cand_source(J, P, M);
         // a range frame scans candidates [beg, end); the node's states are counted by its first range
         const int rbeg = fr[2], rend = fr[3];
@@ -1417,6 +1417,7 @@ __device__ __forceinline__ int split_frame_once(const JobDesc *jobs, const int32
 
 // A split frame with at most this many candidates is expanded by one lane.
 constexpr int SPLIT_LANE_MAX = 8;
+static_assert(SPLIT_LANE_MAX <= 32, "a lane keeps its frame's survivors in one 32-bit mask");
 
 // Frames of candidates a child of position depth + 1 takes: one, or one per
 // SPLIT_RANGE candidates when its list is longer (JOB_LONG_LISTS pairs only).
