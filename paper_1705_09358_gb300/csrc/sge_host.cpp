@@ -282,6 +282,7 @@ struct TargetRec {
     int maxdeg = 0;                // longest out- or in-row
     std::vector<int32_t> labs_h;   // host copy of the distinct labels (ascending)
     DevBuf lbk;            // large targets: label buckets (vertices, their degrees, bucket starts)
+    DevBuf ldm;            // small undirected targets: label-degree masks
     TargetView view() const {
         TargetView v;
         v.n = n;
@@ -305,16 +306,17 @@ struct TargetRec {
         v.lbuck = lbk.p ? lbk.as<int32_t>() : nullptr;
         v.lbdeg = lbk.p ? lbk.as<int32_t>() + n : nullptr;
         v.lbstart = lbk.p ? lbk.as<int32_t>() + 2 * (size_t)n : nullptr;
+        v.ldm = ldm.p ? ldm.as<uint64_t>() : nullptr;
         return v;
     }
     void use_cache(BlockCache *c) {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
-                          &hub_list, &ltab, &lbk})
+                          &hub_list, &ltab, &lbk, &ldm})
             b->cache = c;
     }
     void release() {
         for (DevBuf *b : {&rowptr, &col, &elab, &irowptr, &icol, &ielab, &vld, &indeg, &adj, &hub_slot, &hub_bits,
-                          &hub_list, &ltab, &lbk})
+                          &hub_list, &ltab, &lbk, &ldm})
             b->release();
     }
     ~TargetRec() { release(); }
@@ -2083,6 +2085,13 @@ sge_status sge_load_target(sge_ctx *ctx, int32_t n, int64_t m, const int32_t *sr
             CK(launch_label_nbmax(T->rowptr.as<int32_t>(), T->col.as<int32_t>(), T->vld.as<int2>(),
                                   I.fill_out.as<int32_t>(), n, (int)L, T->ltab.as<int32_t>() + T->ltab_off, st),
                "label table");
+            const long long ldm_words = L * LDM_DEGREES * T->dw;
+            if (n <= LDM_MAX_N && ldm_words <= LDM_MAX_WORDS) {
+                CK(T->ldm.ensure((size_t)ldm_words * 8), "alloc label-degree masks");
+                CK(launch_label_degree_masks(T->vld.as<int2>(), n, T->ltab.as<int32_t>(), (int)L, T->dw,
+                                             T->ldm.as<uint64_t>(), st),
+                   "label-degree masks");
+            }
             if (n > BITSET_MAX_N) {
                 // label buckets: vertices by label index, descending degree within a label, so that
                 // a pattern vertex's initial domain is one bucket prefix (domain initialisation then

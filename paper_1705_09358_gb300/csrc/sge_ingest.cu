@@ -233,7 +233,40 @@ __global__ void __launch_bounds__(IB) k_label_nbmax(const int32_t *rowptr, const
         }
 }
 
+// Label-degree masks: one warp per (label index, degree threshold, 64-vertex word), two
+// ballots over the word's vertices.
+__global__ void __launch_bounds__(IB) k_label_degree_masks(const int2 *vld, int n, const int32_t *labs, long long units,
+                                                           int dw, uint64_t *ldm) {
+    const int lane = threadIdx.x & 31;
+    const long long u = (blockIdx.x * (long long)IB + threadIdx.x) >> 5;
+    if (u >= units) return;
+    const int q = (int)(u % dw);
+    const long long ld = u / dw;
+    const int d = (int)(ld % LDM_DEGREES), l = (int)(ld / LDM_DEGREES);
+    const int lab = labs[l];
+    unsigned long long word = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int t = q * 64 + h * 32 + lane;
+        bool ok = false;
+        if (t < n) {
+            const int2 x = vld[t];
+            ok = x.x == lab && x.y >= d;
+        }
+        word |= (unsigned long long)__ballot_sync(0xffffffffu, ok) << (32 * h);
+    }
+    if (lane == 0) ldm[u] = word;
+}
+
 }  // namespace
+
+cudaError_t launch_label_degree_masks(const int2 *vld, int n, const int32_t *labs, int nlab, int dw, uint64_t *ldm,
+                                      cudaStream_t st) {
+    const long long units = (long long)nlab * LDM_DEGREES * dw;
+    if (units <= 0) return cudaSuccess;
+    k_label_degree_masks<<<blocks_for(units * 32, IB), IB, 0, st>>>(vld, n, labs, units, dw, ldm);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld, const int32_t *lidx, int n,
                                int nlab, int32_t *nbmax, cudaStream_t st) {

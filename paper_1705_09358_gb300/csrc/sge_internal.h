@@ -101,7 +101,15 @@ struct TargetView {
     const int32_t *lbuck;
     const int32_t *lbdeg;
     const int32_t *lbstart;
+    // small undirected targets: per label index l and degree threshold d < LDM_DEGREES, the dw-word
+    // mask of the vertices with label l and degree at least d, at ldm[(l * LDM_DEGREES + d) * dw];
+    // null otherwise.  Domain initialisation without the neighbour-label test copies a row.
+    const uint64_t *ldm;
 };
+
+constexpr int LDM_DEGREES = 17;          // degree thresholds 0..16 in a target's label-degree masks
+constexpr int LDM_MAX_N = 4096;          // targets up to this many vertices get the masks ...
+constexpr long long LDM_MAX_WORDS = 1ll << 18;   // ... when they take at most this many words
 
 struct PatternView {
     int32_t k;
@@ -278,6 +286,9 @@ cudaError_t launch_ingest_degree(const int32_t *rowptr, int n, int32_t *deg, cud
 cudaError_t launch_ingest_maxdeg(const int32_t *rowptr, int n, int32_t *maxdeg, cudaStream_t st);
 cudaError_t launch_ingest_bits(const int32_t *rowptr, const int32_t *col, int n, int dw, uint64_t *bits,
                                cudaStream_t st);
+// The label-degree masks of TargetView::ldm for the nlab labels labs[] (vld: {label, degree}).
+cudaError_t launch_label_degree_masks(const int2 *vld, int n, const int32_t *labs, int nlab, int dw, uint64_t *ldm,
+                                      cudaStream_t st);
 // nbmax[lidx[y] * n + t] = max deg(y) over the neighbours y of t (nbmax zeroed first).
 cudaError_t launch_label_nbmax(const int32_t *rowptr, const int32_t *col, const int2 *vld, const int32_t *lidx, int n,
                                int nlab, int32_t *nbmax, cudaStream_t st);

@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init_buckets(const JobDesc *jo
 }
 
 constexpr int INIT_WORDS_PER_WARP = 32;   // most consecutive filter words one warp of k_domain_init writes
+static_assert(INIT_WORDS_PER_WARP <= 32, "k_domain_init copies a warp's words one per lane");
 
 __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, const long long *unit_off, int njobs,
                                                        long long nunits, int wpw) {
@@ -274,12 +275,53 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
     // k x dw < 2^15 units, so 32-bit arithmetic).  The job's fields are read once per job
     // and the vertex's once per vertex, not once per word.
     int j = find_job(unit_off, njobs, u0);
+    {
+        // when every word of the warp's range is a copy of a label-degree mask row (see
+        // below), the lanes copy one word each at once instead of the warp stepping word by word
+        const long long u = u0 + lane;
+        bool copyable = true;
+        uint64_t *dst = nullptr;
+        uint64_t word = 0;
+        if (u < nunits && u < u0 + wpw) {
+            int jl = j;
+            while (jl + 1 < njobs && unit_off[jl + 1] <= u) ++jl;
+            const JobDesc &J = jobs[jl];
+            if (J.filt != nullptr && J.t.lbuck == nullptr) {
+                const bool nbc = (J.flags & JOB_RIDS) && !(J.flags & JOB_ELAB) && J.t.nbmax != nullptr &&
+                                 J.plidx != nullptr;
+                const int dwl = J.t.dw, local = (int)(u - unit_off[jl]);
+                const int vl = local / dwl, ql = local - vl * dwl;
+                const int odl = J.p.odeg[vl];
+                if (nbc || (J.flags & JOB_DIRECTED) || J.t.ldm == nullptr || odl >= LDM_DEGREES) {
+                    copyable = false;
+                } else {
+                    const int labl = J.p.lab[vl];
+                    int lo = 0, hi = J.t.nlab;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (__ldg(J.t.labs + mid) < labl) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < J.t.nlab && __ldg(J.t.labs + lo) == labl)
+                        word = __ldg(J.t.ldm + ((size_t)lo * LDM_DEGREES + odl) * dwl + ql);
+                    dst = J.filt + (size_t)vl * dwl + ql;
+                }
+            }
+        }
+        if (__all_sync(FULL, copyable)) {
+            if (dst != nullptr) *dst = word;
+            return;
+        }
+    }
     int jcur = -1, v = -1, q = 0, vcur = -1;
     bool skip = true, DIR = false, nbcheck = false;
     int dw = 1, n = 0, lab = 0, od = 0, id = 0;
     const int2 *vld = nullptr;
     const int32_t *indeg = nullptr;
     uint64_t *filt = nullptr;
+    // without the neighbour test, D(v) initialised = the target's label-degree mask row of
+    // (lab(v), deg(v)) when it has one: a copy (mrow null and mempty: lab(v) absent)
+    const uint64_t *mrow = nullptr;
+    bool mempty = false;
     for (long long u = u0; u < u0 + wpw && u < nunits; ++u) {
         while (j + 1 < njobs && unit_off[j + 1] <= u) ++j;
         const JobDesc &J = jobs[j];
@@ -313,6 +355,23 @@ __global__ void __launch_bounds__(BLOCK) k_domain_init(const JobDesc *jobs, cons
             lab = J.p.lab[v];
             od = J.p.odeg[v];
             id = DIR ? J.p.ideg[v] : 0;
+            mrow = nullptr;
+            mempty = false;
+            if (!nbcheck && !DIR && J.t.ldm != nullptr && od < LDM_DEGREES) {
+                int lo = 0, hi = J.t.nlab;   // lab(v)'s index among the target's labels
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(J.t.labs + mid) < lab) lo = mid + 1; else hi = mid;
+                }
+                if (lo < J.t.nlab && __ldg(J.t.labs + lo) == lab)
+                    mrow = J.t.ldm + ((size_t)lo * LDM_DEGREES + od) * dw;
+                else
+                    mempty = true;
+            }
+        }
+        if (mrow != nullptr || mempty) {
+            if (lane == 0) filt[(size_t)v * dw + q] = mempty ? 0ull : __ldg(mrow + q);
+            continue;
         }
         unsigned long long word = 0;
 #pragma unroll
