@@ -715,6 +715,7 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const 
 // slots per warp step so that a candidate with a long row is checked by the
 // whole warp.
 constexpr int FIXPOINT_BIG_BLOCK = 1024;   // threads per block of k_domain_fixpoint when pairs are few
+constexpr int FIXPOINT_SMALL_BLOCK = 128;  // ... and when they are many
 constexpr int FP_CHUNK = 1024;             // domain words scanned at once by k_domain_fixpoint
 
 // Exclusive scan of one int per thread over the block (up to 1024 threads);
@@ -3000,8 +3001,10 @@ cudaError_t launch_domain_fixpoint(const JobDesc *jobs, int njobs, const long lo
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     // few pairs: one large block each, so that they still fill the device; many pairs:
-    // as many blocks as are resident at once, each taking pairs from the counter
-    const int threads = njobs < sms * 4 ? FIXPOINT_BIG_BLOCK : BLOCK;
+    // blocks of four warps (eight pairs in flight per SM; 256 threads measured 3% slower and
+    // 64 threads 15% slower on 196,000 molecule pairs), as many as are resident at once,
+    // each taking pairs from the counter
+    const int threads = njobs < sms * 4 ? FIXPOINT_BIG_BLOCK : FIXPOINT_SMALL_BLOCK;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_domain_fixpoint, threads, 0);
     if (e != cudaSuccess) return e;
