@@ -372,8 +372,8 @@ def cl100k_queries(pool, count: int) -> list:
 
 
 def oracle_throughput(pool, cl100k_patterns) -> dict:
-    """The benchmark's throughput plan for the batched and served workloads: the oracle as it
-    stands, one instance per thread, spread over every host core of the GPU machine."""
+    """The CPU throughput baseline of the batched and served workloads: the oracle as it
+    stands, one instance per thread, spread over every host core."""
     cores = host_cpu()["nproc"]
     out = {}
     pairs = [(ti, pi) for ti in range(200) for pi in range(1000)]
