@@ -403,6 +403,7 @@ struct Workspace {
     std::vector<std::vector<PosInfo>> hjpos;   // per job: its RI-DS position tables, reused
     std::vector<std::vector<BackEdge>> hjback;
     std::vector<long long> hri_off;        // per pattern id: offsets of its RI tables in this call
+    std::vector<int> hri_rep;              // per pattern id: a job of that pattern in this call (-1 after)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;   // search kernel, split kernel
     cudaStream_t bound = nullptr;
 #define SGE_WS_BUFFERS                                                                                             \
@@ -721,11 +722,11 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     std::vector<Job> &jobs = W.hjobs;   // kept across calls (no fresh pages)
     if (jobs.size() < (size_t)nj) jobs.resize((size_t)nj);
     bool directed = false, any_elab = false;
-    int kmax = 1, nmax = 1;
+    int kmax = 1, nmax = 1, max_pid = 0;
     std::mutex red;   // merges the threads' partial maxima
     parallel_for(nj, [&](int q0, int q1) {
         bool el = false;
-        int km = 1, nm = 1;
+        int km = 1, nm = 1, mp = 0;
         for (int q = q0; q < q1; ++q) {
             Job &J = jobs[q];
             J.filt_off = -1;
@@ -741,6 +742,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             }
             J.algo = algo;
             J.active = J.p->k > 0 && J.p->k <= J.t->n;
+            mp = std::max(mp, reqs[J.pair].pid);
             if (J.active) {
                 km = std::max(km, J.p->k);
                 nm = std::max(nm, J.t->n);
@@ -750,6 +752,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         std::lock_guard<std::mutex> g(red);
         kmax = std::max(kmax, km);
         nmax = std::max(nmax, nm);
+        max_pid = std::max(max_pid, mp);
         any_elab = any_elab || el;
     });
     if (nj > 0) directed = jobs[0].t->directed;   // (a group holds pairs of one directedness)
@@ -1101,8 +1104,6 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     std::vector<int> fidx(nj, -1);
     for (int x = 0; x < nf; ++x) fidx[fjobs[x]] = x;
     // an RI pattern's tables are appended once per call: their offsets, by pattern id
-    int max_pid = 0;
-    for (int q = 0; q < nj; ++q) max_pid = std::max(max_pid, reqs[jobs[q].pair].pid);
     std::vector<long long> &ri_off = W.hri_off;   // [pid]: pos offset, back offset (-1: not yet)
     if (ri_off.size() < 2 * ((size_t)max_pid + 1)) ri_off.resize(2 * ((size_t)max_pid + 1), -1);
     std::vector<int> ri_seen;
@@ -1111,8 +1112,7 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
     // threads, into per-job vectors (kept in the workspace); they are appended in job order below
     std::vector<std::vector<PosInfo>> &jpos = W.hjpos;
     std::vector<std::vector<BackEdge>> &jback = W.hjback;
-    bool any_rids_job = false;
-    for (int q = 0; q < nj && !any_rids_job; ++q) any_rids_job = jobs[q].active && jobs[q].algo != SGE_RI;
+    const bool any_rids_job = algo != SGE_RI;   // (every pair of a call has the call's variant)
     if (any_rids_job && jpos.size() < (size_t)nj) {
         jpos.resize((size_t)nj);
         jback.resize((size_t)nj);
@@ -1130,7 +1130,37 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
         for (int q = 0; q < nj; ++q) act += jobs[q].active && jobs[q].algo != SGE_RI;
         std::fprintf(stderr, "[sge] RI-DS orderings of %d live pairs built at %.3f ms\n", act, now_ms() - t_start);
     }
-    for (int q = 0; q < nj; ++q) {
+    if (algo == SGE_RI) {
+        // the distinct patterns' tables: a job of each pattern is noted on several threads
+        // (any job will do), the tables appended by pattern id, then every job's offsets set
+        std::vector<int> &rep = W.hri_rep;   // [pid]: a job of that pattern, or -1
+        if (rep.size() < (size_t)max_pid + 1) rep.resize((size_t)max_pid + 1, -1);
+        parallel_for(nj, [&](int q0, int q1) {
+            for (int q = q0; q < q1; ++q)
+                if (jobs[q].active)   // (threads may note different jobs of one pattern: any is valid)
+                    __atomic_store_n(&rep[(size_t)reqs[jobs[q].pair].pid], q, __ATOMIC_RELAXED);
+        });
+        for (int pid = 0; pid <= max_pid; ++pid) {
+            const int q = rep[(size_t)pid];
+            if (q < 0) continue;
+            rep[(size_t)pid] = -1;
+            const PatternRec *P = jobs[q].p;
+            ri_off[2 * (size_t)pid] = (long long)pos.size();
+            ri_off[2 * (size_t)pid + 1] = (long long)back.size();
+            pos.insert(pos.end(), P->ri_pos.begin(), P->ri_pos.end());
+            back.insert(back.end(), P->ri_back.begin(), P->ri_back.end());
+            ri_seen.push_back(pid);
+        }
+        parallel_for(nj, [&](int q0, int q1) {
+            for (int q = q0; q < q1; ++q) {
+                if (!jobs[q].active) continue;
+                const size_t pid = (size_t)reqs[jobs[q].pair].pid;
+                pos_off[q] = ri_off[2 * pid];
+                back_off[q] = ri_off[2 * pid + 1];
+            }
+        });
+    }
+    for (int q = 0; q < nj && algo != SGE_RI; ++q) {
         Job &J = jobs[q];
         if (!J.active) continue;
         if (J.algo == SGE_RI) {
