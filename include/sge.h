@@ -89,9 +89,10 @@ typedef struct {
                                   SGE_DOMAIN_SWEEPS = sweeps over the whole device under a host
                                   loop; SGE_DOMAIN_BLOCKS = each pair's whole fixpoint in one block
                                   of one launch (targets of at most 16384 vertices: word by word;
-                                  larger ones: over candidate lists); 0 = auto: blocks when the
-                                  batch holds at least half as many RI-DS pairs as the device has
-                                  SMs (small targets) or at least 32 (large targets), else sweeps.
+                                  larger ones: over candidate lists); 0 = auto: on targets of at
+                                  most 16384 vertices word-by-word blocks from half as many RI-DS
+                                  pairs as the device has SMs, candidate-list blocks from 32 pairs,
+                                  else sweeps; on larger targets candidate-list blocks always.
                                   All reach the same fixpoint. */
     int32_t frontier_kib;      /* size of each of the breadth-first split's two frontier buffers
                                   in KiB (default 524288 = 512 MiB); a split level whose children

@@ -42,7 +42,9 @@ constexpr long long CAND_MAX = 1ll << 28;   // most listed domain candidates per
 constexpr int ROOT_CHUNK = 1024;                 // root candidates per root range frame
 constexpr int BLOCK_FIXPOINT_MAX_N = 16384;      // auto domain mode: in-block fixpoint for targets up to this
 constexpr long long LABEL_TABLE_MAX = 1ll << 26; // most (vertex, label) entries of a target's degree table
-constexpr int LIST_FIXPOINT_MIN_JOBS = 32;      // auto domain mode: in-block fixpoint over lists from this many pairs
+constexpr int LIST_FIXPOINT_MIN_JOBS = 32;      // auto domain mode, small targets: in-block fixpoint over lists from
+                                                 // this many pairs (large targets: always; on the 100k-vertex target it
+                                                 // beat the sweeps from 1 to 32 pairs)
 
 // Opt-in phase trace on stderr (SGE_TRACE=1): sizes and timings of each launch group.
 // SGE_TRACE: unset or "0" off; "errors" prints only failures; anything else
@@ -973,7 +975,8 @@ sge_status run_group(sge_ctx *ctx, Workspace &W, cudaStream_t st, const std::vec
             // many RI-DS pairs on large targets: each pair's whole fixpoint in one block, walking
             // the candidate lists (no host round trip per sweep)
             const bool list_blocks = cand_mode && (o.domain_fixpoint == SGE_DOMAIN_BLOCKS ||
-                                                   (o.domain_fixpoint == SGE_DOMAIN_AUTO && nrids >= LIST_FIXPOINT_MIN_JOBS));
+                                                   (o.domain_fixpoint == SGE_DOMAIN_AUTO &&
+                                                    (!small_targets || nrids >= LIST_FIXPOINT_MIN_JOBS)));
             if (list_blocks) {
                 std::vector<long long> cs((size_t)nverts * 2);
                 std::copy(cstart.begin(), cstart.end(), cs.begin());
