@@ -19,6 +19,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <exception>
+#include <functional>
 #include <map>
 #include <memory>
 #include <new>
@@ -27,6 +29,8 @@
 #include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <unistd.h>
 
 using namespace sge;
 
@@ -660,24 +664,106 @@ struct PairReq {
     PatternRec *p = nullptr;
 };
 
-// Runs body(begin, end) over [0, n) split across up to 8 host threads, each with
-// at least `min_per_thread` items (16384 by default: batches of many thousands of
-// cheap pairs), else inline.
+constexpr int HOST_THREADS_MAX = 16;  // host threads of one parallel_for, the caller's included
+
+// Host worker threads for parallel_for, started once per process: creating and
+// joining threads for every loop cost tens of microseconds per thread, paid several
+// times by each large batched call.  One parallel_for at a time runs on the pool
+// (`busy`); one that finds it taken, by another host thread or from inside a loop
+// body, starts threads of its own.  A forked child, which inherits the pool's
+// memory but not its threads, starts a pool of its own.
+class HostPool {
+  public:
+    explicit HostPool(int nworkers) {
+        for (int i = 1; i <= nworkers; ++i) std::thread([this, i] { worker(i); }).detach();
+    }
+    std::atomic<bool> busy{false};
+    // runs task(0) on the calling thread and task(1) .. task(nt - 1) on workers
+    // 1 .. nt - 1 (nt - 1 <= nworkers), returning when all have finished
+    void run(int nt, const std::function<void(int)> &t) {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            task_ = &t;
+            want_ = left_ = nt - 1;
+            ++gen_;
+        }
+        go_.notify_all();
+        std::exception_ptr err;   // (the workers still use `t`: wait for them before rethrowing)
+        try {
+            t(0);
+        } catch (...) {
+            err = std::current_exception();
+        }
+        std::unique_lock<std::mutex> lk(m_);
+        fin_.wait(lk, [&] { return left_ == 0; });
+        if (err) std::rethrow_exception(err);
+    }
+
+  private:
+    // Worker i takes part in a run if i <= want_.  A run cannot end (left_ > 0) before
+    // each of its workers has seen its generation, so none skips one it belongs to.
+    void worker(int i) {
+        unsigned long long seen = 0;
+        std::unique_lock<std::mutex> lk(m_);
+        for (;;) {
+            go_.wait(lk, [&] { return gen_ != seen; });
+            seen = gen_;
+            if (i > want_) continue;
+            const std::function<void(int)> *t = task_;
+            lk.unlock();
+            (*t)(i);
+            lk.lock();
+            if (--left_ == 0) fin_.notify_one();
+        }
+    }
+    std::mutex m_;
+    std::condition_variable go_, fin_;
+    const std::function<void(int)> *task_ = nullptr;
+    int want_ = 0, left_ = 0;
+    unsigned long long gen_ = 0;
+};
+
+HostPool *host_pool() {
+    static std::mutex mk;
+    static HostPool *pool = nullptr;   // never destroyed: its detached workers outlive static teardown
+    static pid_t owner = 0;
+    std::lock_guard<std::mutex> lk(mk);
+    if (pool == nullptr || owner != getpid()) {
+        pool = new HostPool(HOST_THREADS_MAX - 1);
+        owner = getpid();
+    }
+    return pool;
+}
+
+// Runs body(begin, end) over [0, n) split across up to HOST_THREADS_MAX host threads
+// (no more than the machine has), each with at least `min_per_thread` items (16384 by
+// default: batches of many thousands of cheap pairs), else inline.
 template <class F>
 void parallel_for(int n, F body, int min_per_thread = 16384) {
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::min(std::min(8, hw), n / min_per_thread);
+    const int nt = std::min(std::min(HOST_THREADS_MAX, hw), n / min_per_thread);
     if (nt <= 1) {
         body(0, n);
         return;
     }
-    std::vector<std::thread> th;
     const int chunk = (n + nt - 1) / nt;
-    for (int t = 1; t < nt; ++t) {
+    const std::function<void(int)> slice = [&](int t) {
         const int b = t * chunk, e = std::min(n, b + chunk);
-        if (b < e) th.emplace_back([&body, b, e] { body(b, e); });
+        if (b < e) body(b, e);
+    };
+    HostPool *pool = host_pool();
+    bool idle = false;
+    if (pool->busy.compare_exchange_strong(idle, true)) {
+        struct Release {
+            std::atomic<bool> &b;
+            ~Release() { b.store(false); }
+        } release{pool->busy};
+        pool->run(nt, slice);
+        return;
     }
-    body(0, std::min(n, chunk));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back([&slice, t] { slice(t); });
+    slice(0);
     for (auto &x : th) x.join();
 }
 

@@ -717,6 +717,8 @@ __global__ void __launch_bounds__(BLOCK) k_domain_fc(const JobDesc *jobs, const 
 constexpr int FIXPOINT_BIG_BLOCK = 1024;   // threads per block of k_domain_fixpoint when pairs are few
 constexpr int FIXPOINT_SMALL_BLOCK = 128;  // ... and when they are many
 constexpr int FP_CHUNK = 1024;             // domain words scanned at once by k_domain_fixpoint
+static_assert(FP_CHUNK % FIXPOINT_BIG_BLOCK == 0 && FP_CHUNK % FIXPOINT_SMALL_BLOCK == 0,
+              "a fixpoint block scans FP_CHUNK words in whole rounds of one word per thread");
 
 // Exclusive scan of one int per thread over the block (up to 1024 threads);
 // `total` receives the block's sum.  wsum: 32 ints of shared memory.
@@ -746,18 +748,27 @@ __device__ __forceinline__ int block_scan_int(int x, int *wsum, int &total) {
     return before + incl - x;
 }
 
-// Position of the r-th (0-based) set bit of w (r < popcount(w)).
+// Position of the r-th (0-based) set bit of w (r < popcount(w)): the window that
+// holds it is halved six times, each step comparing r with the low half's popcount.
 __device__ __forceinline__ int select_bit(uint64_t w, int r) {
     int base = 0;
     uint32_t h = (uint32_t)w;
-    const int pl = __popc(h);
-    if (r >= pl) {
-        r -= pl;
+    int c = __popc(h);
+    if (r >= c) {
+        r -= c;
         h = (uint32_t)(w >> 32);
         base = 32;
     }
-    for (int i = 0; i < r; ++i) h &= h - 1;
-    return base + __ffs(h) - 1;
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        c = __popc(h & ((1u << half) - 1u));
+        if (r >= c) {
+            r -= c;
+            h >>= half;
+            base += half;
+        }
+    }
+    return base;
 }
 
 __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const JobDesc *jobs, int njobs,
@@ -816,9 +827,11 @@ __global__ void __launch_bounds__(FIXPOINT_BIG_BLOCK, 1) k_domain_fixpoint(const
                     // popcounts, and give each thread the next set bit, so the candidates of a
                     // dense word are checked in parallel rather than by one thread in turn
                     const long long units = (long long)n_d * dw;
-                    const int ipt = FP_CHUNK / blockDim.x;   // words per thread in the scan
                     for (long long u0 = 0; u0 < units; u0 += FP_CHUNK) {
                         const int nw_c = (int)min((long long)FP_CHUNK, units - u0);
+                        // words per thread in the scan: as few as the chunk needs (FP_CHUNK is a
+                        // multiple of the block size, so tid * ipt + r stays below FP_CHUNK)
+                        const int ipt = (nw_c + (int)blockDim.x - 1) / (int)blockDim.x;
                         int cnt = 0;
                         for (int r = 0; r < ipt; ++r) {
                             const int iw = tid * ipt + r;

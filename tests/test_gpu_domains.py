@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from brute import plant, random_graph
+from brute import plant, plant_connected, random_graph
 from gen import configs
 from gpu_common import counters, engine, golden, golden_counters, workload
 
@@ -46,6 +46,44 @@ def test_block_fixpoint_on_tiny_random_cases(directed):
             for mode in (SWEEPS, BLOCKS):
                 rc, rows = E.count_batch(tids, pids, algo=algo, domain_fixpoint=mode)
                 assert [counters(r) for r in rows] == want, (algo, mode)
+    finally:
+        _unload(E, tids, pids)
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_block_fixpoint_on_many_small_random_cases(directed):
+    """A batch of 1,000 pairs: enough that the fixpoint runs in blocks of four warps, as many as
+    are resident, each taking pairs from the counter; 100 random labelled pairs (one to four
+    domain words per pattern vertex), each repeated ten times across the batch, every RI-DS
+    variant, against the oracle and the sweep schedule."""
+    E = engine()
+    rng = np.random.default_rng(191 + directed)
+    pairs = []
+    for i in range(100):
+        if i % 2 == 0:   # one domain word per pattern vertex
+            n = int(rng.integers(4, 16))
+            t = random_graph(rng, n, float(rng.uniform(0.2, 0.8)), int(rng.integers(1, 4)),
+                             int(rng.integers(1, 3)), directed)
+            p = plant(rng, t, int(rng.integers(2, min(n, 6) + 1)), float(rng.uniform(0.3, 1.0)))
+        else:            # two to four words: sparse targets, connected patterns
+            n = int(rng.integers(65, 257))
+            t = random_graph(rng, n, float(rng.uniform(0.02, 0.05)), int(rng.integers(2, 5)),
+                             int(rng.integers(1, 3)), directed)
+            p = plant_connected(rng, t, int(rng.integers(3, 9)))
+        pairs.append((t, p))
+    tids = [E.load_target(t) for t, _ in pairs]
+    pids = [E.load_pattern(p) for _, p in pairs]
+    order = np.tile(np.arange(len(pairs)), 10)
+    rng.shuffle(order)
+    T = np.array(tids, np.int32)[order]
+    P = np.array(pids, np.int32)[order]
+    try:
+        for algo in (1, 2, 3):
+            want = [counters(oracle.run(t, p, algo)) for t, p in pairs]
+            rc, blocks = E.count_batch(T, P, algo=algo, domain_fixpoint=BLOCKS)
+            assert [counters(r) for r in blocks] == [want[i] for i in order], algo
+            rc, sweeps = E.count_batch(T, P, algo=algo, domain_fixpoint=SWEEPS)
+            assert [counters(r) for r in sweeps] == [want[i] for i in order], algo
     finally:
         _unload(E, tids, pids)
 
