@@ -19,9 +19,9 @@ pytestmark = pytest.mark.gpu
 ALGOS = (0, 1, 2, 3)
 
 
-def _empty(n: int, labels=None) -> Graph:
+def _empty(n: int, labels=None, directed: bool = False) -> Graph:
     vl = np.zeros(n, np.int32) if labels is None else np.asarray(labels, np.int32)
-    return Graph(n, np.zeros(0, np.int32), np.zeros(0, np.int32), vl)
+    return Graph(n, np.zeros(0, np.int32), np.zeros(0, np.int32), vl, None, directed)
 
 
 def _unload(E, tids, pids):
@@ -55,6 +55,34 @@ def test_largest_pattern_closed_forms():
         _check(E, t, p, matches=m)
 
 
+def _cycle_directed(n: int) -> Graph:
+    return edges_graph(n, [(i, (i + 1) % n) for i in range(n)], directed=True)
+
+
+def _path_directed(n: int) -> Graph:
+    return edges_graph(n, [(i, i + 1) for i in range(n - 1)], directed=True)
+
+
+def test_largest_pattern_match_lists():
+    """Full sorted match lists of a 128-vertex pattern (the match sink at its widest rows): the
+    path in the 200-cycle (400 matches) on both kernels, and the directed path in the directed
+    200-cycle (one direction: 200 matches)."""
+    E = engine()
+    for t, p, m, kernels in [(cycle(200), path(128), 400, (1, 2)),
+                             (_cycle_directed(200), _path_directed(128), 200, (1,))]:
+        tid, pid = E.load_target(t), E.load_pattern(p)
+        try:
+            for algo in (0, 3):
+                want = oracle.run(t, p, algo, want_matches=True)
+                assert want["matches"] == m and want["match_list"].shape == (m, 128)
+                for kern in kernels:
+                    got = E.enumerate(tid, pid, algo=algo, kernel=kern)
+                    assert np.array_equal(got["match_list"].reshape(-1, 128), want["match_list"]), (algo, kern)
+                    assert counters(got) == counters(want), (algo, kern)
+        finally:
+            _unload(E, [tid], [pid])
+
+
 def test_pattern_of_129_vertices_is_refused():
     E = engine()
     with pytest.raises(sge.SgeError) as err:
@@ -74,15 +102,20 @@ def test_empty_and_edgeless_targets():
     _check(E, edgeless, path(2), matches=0)
 
 
-def test_batch_mixing_oversized_empty_and_ordinary_pairs():
+@pytest.mark.parametrize("directed", [False, True])
+def test_batch_mixing_oversized_empty_and_ordinary_pairs(directed):
     """One batched call whose pairs include patterns with more vertices than their target, the
     empty pattern and ordinary connected patterns on random labelled targets, every variant:
     each row equals the oracle's counters for its own pair."""
     E = engine()
-    rng = np.random.default_rng(4242)
-    targets = [random_graph(rng, int(rng.integers(20, 120)), 0.08, 3, 2) for _ in range(6)]
+    rng = np.random.default_rng(4242 + directed)
+    targets = [random_graph(rng, int(rng.integers(20, 120)), 0.08, 3, 2, directed) for _ in range(6)]
     patterns = [plant_connected(rng, targets[i % 6], int(rng.integers(3, 7))) for i in range(8)]
-    patterns += [complete(30), path(128), _empty(0), edges_graph(2, [(0, 1)], labels=[7, 7])]
+    if directed:
+        patterns += [_cycle_directed(30), _path_directed(128), _empty(0, directed=True),
+                     edges_graph(2, [(0, 1)], labels=[7, 7], directed=True)]
+    else:
+        patterns += [complete(30), path(128), _empty(0), edges_graph(2, [(0, 1)], labels=[7, 7])]
     tids = [E.load_target(t) for t in targets]
     pids = [E.load_pattern(p) for p in patterns]
     pairs = [(i, j) for i in range(len(targets)) for j in range(len(patterns))]
