@@ -126,3 +126,34 @@ def test_batch_mixing_oversized_empty_and_ordinary_pairs(directed):
             assert [counters(r) for r in rows] == want, algo
     finally:
         _unload(E, tids, pids)
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_serving_at_the_limits(directed):
+    """Served queries of every kind at once, on two targets (160 and 40 vertices): ordinary
+    patterns, a 128-vertex pattern (larger than the small target), the empty pattern and an
+    edgeless one, all four variants: each result equals the oracle's counters for its pair."""
+    E = engine()
+    rng = np.random.default_rng(777 + directed)
+    targets = [random_graph(rng, 160, 0.05, 3, 2, directed), random_graph(rng, 40, 0.1, 3, 2, directed)]
+    pats = [plant_connected(rng, targets[i % 2], int(rng.integers(3, 8))) for i in range(12)]
+    if directed:
+        pats += [_path_directed(128), _empty(0, directed=True), _empty(3, [0, 1, 2], True)]
+    else:
+        pats += [path(128), _empty(0), _empty(3, [0, 1, 2])]
+    tids = [E.load_target(t) for t in targets]
+    pids = [E.load_pattern(p) for p in pats]
+    try:
+        subs = []
+        for rep in range(3):
+            for i in range(len(targets)):
+                for j, pid in enumerate(pids):
+                    algo = (i + j + rep) % 4
+                    subs.append((i, j, algo, E.serve_submit(tids[i], pid, algo=algo)))
+        E.serve_drain()
+        for i, j, algo, tk in subs:
+            r = E.serve_poll(tk)
+            assert r is not None and r["status"] == 0, (i, j, algo, r and r["status"])
+            assert counters(r) == counters(oracle.run(targets[i], pats[j], algo)), (i, j, algo)
+    finally:
+        _unload(E, tids, pids)
