@@ -122,6 +122,28 @@ def test_medium_directed(seed):
     _check_pair(engine(), t, p, kernels=(0,))
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_medium_directed_labelled_match_lists(seed):
+    """Full sorted match lists on directed targets with edge labels (several bitset words, ragged
+    tails), every variant."""
+    rng = np.random.default_rng(61000 + seed)
+    n = int(rng.integers(100, 330))
+    t = random_graph(rng, n, 0.04, 2, 3, directed=True)
+    p = plant_connected(rng, t, int(rng.integers(3, 7)))
+    _check_pair(engine(), t, p, kernels=(0,), want_list=True)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_medium_match_lists_both_kernels(seed):
+    """Full sorted match lists on undirected vertex-labelled targets (several bitset words,
+    ragged tails), the CSR and the bitset kernel, every variant."""
+    rng = np.random.default_rng(62000 + seed)
+    n = int(rng.integers(100, 330))
+    t = random_graph(rng, n, 0.05, 3, 1)
+    p = plant_connected(rng, t, int(rng.integers(3, 7)))
+    _check_pair(engine(), t, p, kernels=(1, 2), want_list=True)
+
+
 # ------------------------------------------------------------- workload 1
 def test_er1000_full_match_list():
     w = configs.er1000()
