@@ -115,6 +115,28 @@ def test_cl100k_budget_resume():
     assert _table(rows) == want
 
 
+@pytest.mark.parametrize("algo", [0, 3])
+def test_directed_labelled_budget_resume(algo):
+    """A directed, edge-labelled batch (the CSR kernel's in/out rows and direction-aware back-edge
+    checks) cut by a state budget below the persistent kernel (split depth 1) and resumed to the
+    end: every pair's counters equal the oracle's."""
+    import oracle
+    from brute import plant_connected, random_graph
+    rng = np.random.default_rng(880)
+    t = random_graph(rng, 300, 0.05, 2, 2, directed=True)
+    pats = [plant_connected(rng, t, int(rng.integers(4, 8))) for _ in range(24)]
+    E = engine()
+    tid = E.load_target(t)
+    pids = [E.load_pattern(p) for p in pats]
+    want = [counters(oracle.run(t, p, algo)) for p in pats]
+    budget = max(w[1] for w in want) // 5
+    rc, rows, blob = E.count_batch_ckpt([tid] * len(pids), pids, algo=algo, split_depth=1, state_budget=budget)
+    assert rc == BUDGET and blob is not None
+    rows, calls = _drain(E, blob, state_budget=budget)
+    assert calls >= 1
+    assert _table(rows) == want
+
+
 def test_finished_search_leaves_no_checkpoint():
     E, tid, pids, g = _er2000()
     rc, rows, blob = E.count_batch_ckpt([tid] * 5, pids, algo=3)
