@@ -68,7 +68,7 @@ def test_complete_in_complete(n, k):
     assert r["matches"] == _perm(n, k)
 
 
-@pytest.mark.parametrize("k", [3, 4, 7, 12])
+@pytest.mark.parametrize("k", [3, 4, 7, 12, 128])
 def test_cycle_in_itself(k):
     for algo in ALGOS:
         assert oracle.run(cycle(k), cycle(k), algo)["matches"] == 2 * k
@@ -81,10 +81,39 @@ def test_star_in_star(n, k):
         assert oracle.run(star(n), star(k), algo)["matches"] == want
 
 
-@pytest.mark.parametrize("n,k", [(5, 2), (6, 4), (9, 9), (11, 6)])
+@pytest.mark.parametrize("n,k", [(5, 2), (6, 4), (9, 9), (11, 6), (200, 128)])
 def test_path_in_cycle(n, k):
     for algo in ALGOS:
         assert oracle.run(cycle(n), path(k), algo)["matches"] == 2 * n
+
+
+@pytest.mark.parametrize("n,k", [(5, 2), (10, 4), (7, 7), (130, 128)])
+def test_path_in_path(n, k):
+    # a placement of the k-path on the n-path (n - k + 1) times two directions
+    for algo in ALGOS:
+        assert oracle.run(path(n), path(k), algo)["matches"] == 2 * (n - k + 1)
+
+
+@pytest.mark.parametrize("n,k", [(6, 2), (9, 4), (7, 7), (200, 128)])
+def test_directed_path_in_directed_cycle(n, k):
+    # one direction only: a start vertex each
+    c = edges_graph(n, [(i, (i + 1) % n) for i in range(n)], directed=True)
+    pk = edges_graph(k, [(i, i + 1) for i in range(k - 1)], directed=True)
+    for algo in ALGOS:
+        assert oracle.run(c, pk, algo)["matches"] == n
+
+
+@pytest.mark.parametrize("tl,pl", [([0, 0, 0, 1, 1, 1], [0, 0, 1]), ([0, 1, 2, 2, 2], [2, 2, 1]), ([0, 0], [1])])
+def test_labelled_isolated_vertices(tl, pl):
+    # edgeless graphs: each label's pattern vertices go injectively to that label's target vertices
+    t = Graph(len(tl), np.zeros(0, np.int32), np.zeros(0, np.int32), np.array(tl, np.int32))
+    p = Graph(len(pl), np.zeros(0, np.int32), np.zeros(0, np.int32), np.array(pl, np.int32))
+    want = 1
+    for lab in set(pl):
+        a, b = tl.count(lab), pl.count(lab)
+        want *= _perm(a, b) if b <= a else 0
+    for algo in ALGOS:
+        assert oracle.run(t, p, algo)["matches"] == want
 
 
 @pytest.mark.parametrize("n,k", [(6, 3), (7, 2), (5, 5)])
