@@ -103,3 +103,14 @@ def test_search_roofline_follows_the_capture_record():
     assert abs(r["frac"] - r["instructions_per_launch"] / 5e-3 / r["peak"]) < 1e-12
     assert r["traffic"] == int(rec["dram_bytes_per_launch"])
     assert abs(r["instructions_per_search_node"] - r["instructions_per_launch"] / 17e6) < 1e-9
+
+
+def test_capture_record_belongs_to_these_sources():
+    """The ncu counts committed under profiles/ were taken on the kernel and schedule sources as
+    they stand (their SHA-256 is recorded with them), so the bench line's roofline carries
+    measured instruction and traffic counts rather than none."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = bench._measured_record()
+    assert rec, "profiles/search_kernel_traffic.txt was captured on other sources"
+    assert int(rec["warp_instructions_per_launch"]) > 0 and int(rec["dram_bytes_per_launch"]) > 0
